@@ -1,0 +1,427 @@
+/*
+ * FP64 CPU oracle for the D3Q19 lattice Boltzmann time step of Bauer & Ruede,
+ * "An improved lattice Boltzmann D3Q19 method based on an alternative
+ * equilibrium discretization" (arXiv:1803.04937).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * definition of what the GPU library computes.  It is used by the tests, by
+ * the smoke check and by the CPU-baseline leg of the benchmark, never by the
+ * library itself.  It shares no code, tables or headers with the CUDA path.
+ *
+ * Conventions (all lattice units, dx = dt = 1, c_s^2 = 1/3):
+ *   - velocity set: D3Q19 of Sec. 2.3 (rest, 6 faces, 12 edges), built here by
+ *     enumerating {-1,0,1}^3 and keeping |c|^2 <= 2, in this file's own order;
+ *     weights 1/3, 1/18, 1/36 (Sec. 2.3).
+ *   - state: f[((z*ny + y)*nx + x)*19 + q], the post-streaming, pre-collision
+ *     populations f_q(x, t) of Eq. 15.
+ *   - equilibria: standard D3Q19-S = Eq. 14 truncated at second order in u;
+ *     improved D3Q19-I = Eq. 22.  rho0 = 1 (Sec. 2.3, used for all of the
+ *     paper's analysis) or rho0 = rho (the compressible variant below Eq. 14).
+ *   - update: Eq. 15 with the Buick-Greated force F_q = w_q c_q.a / c_s^2 and
+ *     the velocity shift of Eq. 17: rho0 u = sum_q c_q f_q + a/2.
+ *   - TRT (Sec. 3.3 names it; the paper gives no formula): symmetric and
+ *     antisymmetric parts relax with omega+ = 1/tau and omega- = 1/tau-,
+ *     (tau+ - 1/2)(tau- - 1/2) = Lambda; the force is odd in c and takes
+ *     (1 - omega-/2).  With omega- = omega+ this is Eq. 15 exactly.
+ *   - boundaries: periodic, or half-way bounce-back walls at both ends of an
+ *     axis (Sec. 5.1): a population whose link leaves the domain through a
+ *     wall returns to its own cell reversed, f_qbar(x, t+1) = f*_q(x, t).
+ *   - streaming is done by PUSH after collision (the GPU library pulls).
+ *
+ * The adjoint (reverse-mode derivative of one step; not in the paper) is
+ * written as the transpose of the explicitly assembled 19x19 Jacobian of the
+ * collision, composed with the transpose of the streaming permutation.  It
+ * supports rho0 = 1 only.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 19
+
+typedef struct {
+    int nx, ny, nz;
+    int equilibrium;   /* 0: standard D3Q19-S, 1: improved D3Q19-I */
+    int collision;     /* 0: SRT, 1: TRT */
+    int rho0_is_rho;   /* 0: rho0 = 1, 1: rho0 = rho */
+    int wall[3];       /* 1: half-way bounce-back walls at both ends of axis */
+    int nthreads;      /* OpenMP threads (<= 0: library default) */
+    double tau;        /* relaxation time, omega = 1/tau */
+    double trt_magic;  /* Lambda = (tau+ - 1/2)(tau- - 1/2) */
+    double accel[3];   /* body force a */
+} oracle_cfg;
+
+static int C[Q][3];
+static double W[Q];
+static int OPP[Q];
+static int built = 0;
+
+/* D3Q19 velocities and weights (Sec. 2.3). */
+static void build_lattice(void)
+{
+    if (built) return;
+    int q = 0;
+    for (int cx = -1; cx <= 1; ++cx)
+        for (int cy = -1; cy <= 1; ++cy)
+            for (int cz = -1; cz <= 1; ++cz) {
+                int n = cx * cx + cy * cy + cz * cz;
+                if (n > 2) continue;
+                C[q][0] = cx; C[q][1] = cy; C[q][2] = cz;
+                W[q] = (n == 0) ? 1.0 / 3.0 : (n == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+                ++q;
+            }
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b)
+            if (C[a][0] == -C[b][0] && C[a][1] == -C[b][1] && C[a][2] == -C[b][2])
+                OPP[a] = b;
+    built = 1;
+}
+
+void oracle_velocity_set(int *c, double *w, int *opp)
+{
+    build_lattice();
+    for (int q = 0; q < Q; ++q) {
+        for (int i = 0; i < 3; ++i) c[3 * q + i] = C[q][i];
+        w[q] = W[q];
+        opp[q] = OPP[q];
+    }
+}
+
+/* Eq. 14 (second-order part) or Eq. 22, for one cell. */
+static void equilibrium(int kind, double rho, double rho0, const double u[3], double feq[Q])
+{
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int q = 0; q < Q; ++q) {
+        double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
+        int n = C[q][0] * C[q][0] + C[q][1] * C[q][1] + C[q][2] * C[q][2];
+        double bracket;
+        if (kind == 0) {
+            /* D3Q19-S: 3 c.u + 9/2 u_a u_b (c_a c_b - delta_ab / 3) */
+            bracket = 3.0 * cu + 4.5 * cu * cu - 1.5 * uu;
+        } else if (n == 0) {
+            /* D3Q19-I, rest */
+            bracket = -uu;
+        } else if (n == 1) {
+            /* D3Q19-I, faces */
+            bracket = 3.0 * cu - 3.0 * uu + 6.0 * cu * cu;
+        } else {
+            /* D3Q19-I, edges; sum over i of u_i^2 c_qi^2 */
+            double s = 0.0;
+            for (int i = 0; i < 3; ++i) s += u[i] * u[i] * C[q][i] * C[q][i];
+            bracket = 3.0 * cu - 1.5 * s + 4.5 * cu * cu;
+        }
+        feq[q] = W[q] * rho + W[q] * rho0 * bracket;
+    }
+}
+
+/* d feq_q / d u_i at fixed rho, for rho0 = 1 (the derivative of the two
+ * closed forms above, written out by hand). */
+static void equilibrium_du(int kind, const double u[3], double d[Q][3])
+{
+    for (int q = 0; q < Q; ++q) {
+        double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
+        int n = C[q][0] * C[q][0] + C[q][1] * C[q][1] + C[q][2] * C[q][2];
+        for (int i = 0; i < 3; ++i) {
+            double ci = C[q][i];
+            double v;
+            if (kind == 0) v = 3.0 * ci + 9.0 * cu * ci - 3.0 * u[i];
+            else if (n == 0) v = -2.0 * u[i];
+            else if (n == 1) v = 3.0 * ci - 6.0 * u[i] + 12.0 * cu * ci;
+            else v = 3.0 * ci - 3.0 * u[i] * ci * ci + 9.0 * cu * ci;
+            d[q][i] = W[q] * v;
+        }
+    }
+}
+
+void oracle_equilibrium_field(int kind, int rho0_is_rho, long n, const double *rho,
+                              const double *u, double *feq)
+{
+    build_lattice();
+    for (long k = 0; k < n; ++k) {
+        double uk[3] = {u[k], u[n + k], u[2 * n + k]};
+        double rho0 = rho0_is_rho ? rho[k] : 1.0;
+        equilibrium(kind, rho[k], rho0, uk, feq + k * Q);
+    }
+}
+
+static void omegas(const oracle_cfg *cfg, double *wp, double *wm)
+{
+    *wp = 1.0 / cfg->tau;
+    if (cfg->collision == 1) {
+        double tau_minus = 0.5 + cfg->trt_magic / (cfg->tau - 0.5);
+        *wm = 1.0 / tau_minus;
+    } else {
+        *wm = *wp;
+    }
+}
+
+/* Moments of Eq. 16 and Eq. 17 for one cell. */
+static void cell_moments(const oracle_cfg *cfg, const double *f, double *rho, double *rho0, double u[3])
+{
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < Q; ++q) {
+        r += f[q];
+        for (int i = 0; i < 3; ++i) j[i] += C[q][i] * f[q];
+    }
+    double r0 = cfg->rho0_is_rho ? r : 1.0;
+    for (int i = 0; i < 3; ++i) u[i] = (j[i] + 0.5 * cfg->accel[i]) / r0;
+    *rho = r;
+    *rho0 = r0;
+}
+
+/* Post-collision populations of one cell (Eq. 15, or its TRT split). */
+static void collide(const oracle_cfg *cfg, const double *f, double fs[Q])
+{
+    double rho, rho0, u[3], feq[Q], wp, wm;
+    cell_moments(cfg, f, &rho, &rho0, u);
+    equilibrium(cfg->equilibrium, rho, rho0, u, feq);
+    omegas(cfg, &wp, &wm);
+    for (int q = 0; q < Q; ++q) {
+        int o = OPP[q];
+        double F = 3.0 * W[q] * (C[q][0] * cfg->accel[0] + C[q][1] * cfg->accel[1] + C[q][2] * cfg->accel[2]);
+        double fp = 0.5 * (f[q] + f[o]), fm = 0.5 * (f[q] - f[o]);
+        double ep = 0.5 * (feq[q] + feq[o]), em = 0.5 * (feq[q] - feq[o]);
+        if (cfg->collision == 0)
+            fs[q] = f[q] - wp * (f[q] - feq[q]) + (1.0 - 0.5 * wp) * F;
+        else
+            fs[q] = f[q] - wp * (fp - ep) - wm * (fm - em) + (1.0 - 0.5 * wm) * F;
+    }
+}
+
+static long cell_index(const oracle_cfg *cfg, int x, int y, int z)
+{
+    return ((long)z * cfg->ny + y) * (long)cfg->nx + x;
+}
+
+/* Target of the link from (x,y,z) along c_q.  Returns 0 and the wrapped
+ * target cell for a periodic or interior link; returns 1 when the link
+ * crosses a wall (half-way bounce-back). */
+static int link_target(const oracle_cfg *cfg, int x, int y, int z, int q, long *target)
+{
+    int p[3] = {x + C[q][0], y + C[q][1], z + C[q][2]};
+    int n[3] = {cfg->nx, cfg->ny, cfg->nz};
+    for (int i = 0; i < 3; ++i) {
+        if (p[i] < 0 || p[i] >= n[i]) {
+            if (cfg->wall[i]) return 1;
+            p[i] = (p[i] + n[i]) % n[i];
+        }
+    }
+    *target = cell_index(cfg, p[0], p[1], p[2]);
+    return 0;
+}
+
+static void set_threads(const oracle_cfg *cfg)
+{
+#ifdef _OPENMP
+    if (cfg->nthreads > 0) omp_set_num_threads(cfg->nthreads);
+#else
+    (void)cfg;
+#endif
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* f(t=0) = feq(rho, u0): the initialisation without non-equilibrium part. */
+void oracle_init(const oracle_cfg *cfg, const double *rho, const double *u, double *f)
+{
+    build_lattice();
+    long n = (long)cfg->nx * cfg->ny * cfg->nz;
+    for (long k = 0; k < n; ++k) {
+        double uk[3] = {u[k], u[n + k], u[2 * n + k]};
+        double rho0 = cfg->rho0_is_rho ? rho[k] : 1.0;
+        equilibrium(cfg->equilibrium, rho[k], rho0, uk, f + k * Q);
+    }
+}
+
+/* One time step of Eq. 15: collide every cell, then push along c_q. */
+void oracle_step(const oracle_cfg *cfg, const double *f, double *fnew)
+{
+    build_lattice();
+    set_threads(cfg);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < cfg->nz; ++z)
+        for (int y = 0; y < cfg->ny; ++y)
+            for (int x = 0; x < cfg->nx; ++x) {
+                long k = cell_index(cfg, x, y, z);
+                double fs[Q];
+                collide(cfg, f + k * Q, fs);
+                for (int q = 0; q < Q; ++q) {
+                    long t;
+                    if (link_target(cfg, x, y, z, q, &t))
+                        fnew[k * Q + OPP[q]] = fs[q];
+                    else
+                        fnew[t * Q + q] = fs[q];
+                }
+            }
+}
+
+/* rho = sum_q f_q (Eq. 16), u from Eq. 17. */
+void oracle_moments(const oracle_cfg *cfg, const double *f, double *rho, double *u)
+{
+    build_lattice();
+    long n = (long)cfg->nx * cfg->ny * cfg->nz;
+    for (long k = 0; k < n; ++k) {
+        double r, r0, uk[3];
+        cell_moments(cfg, f + k * Q, &r, &r0, uk);
+        rho[k] = r;
+        for (int i = 0; i < 3; ++i) u[i * n + k] = uk[i];
+    }
+}
+
+/* nsteps steps from f = feq(rho, u); returns final rho, u.  Two grids. */
+int oracle_run(const oracle_cfg *cfg, const double *rho_in, const double *u_in, int nsteps,
+               double *rho_out, double *u_out)
+{
+    long n = (long)cfg->nx * cfg->ny * cfg->nz;
+    double *a = (double *)malloc(sizeof(double) * Q * n);
+    double *b = (double *)malloc(sizeof(double) * Q * n);
+    if (!a || !b) { free(a); free(b); return 1; }
+    oracle_init(cfg, rho_in, u_in, a);
+    for (int s = 0; s < nsteps; ++s) {
+        oracle_step(cfg, a, b);
+        double *t = a; a = b; b = t;
+    }
+    oracle_moments(cfg, a, rho_out, u_out);
+    free(a);
+    free(b);
+    return 0;
+}
+
+/* ---------------- adjoint (rho0 = 1) ---------------- */
+
+/* Jacobian J[q][p] = d fs_q / d f_p of the collision of one cell, and the
+ * derivatives of fs with respect to omega+ and omega-. */
+static void collide_jacobian(const oracle_cfg *cfg, const double *f, double J[Q][Q],
+                             double dfs_dwp[Q], double dfs_dwm[Q])
+{
+    double rho, rho0, u[3], feq[Q], du[Q][3], wp, wm, dfeq[Q][Q];
+    cell_moments(cfg, f, &rho, &rho0, u);
+    equilibrium(cfg->equilibrium, rho, rho0, u, feq);
+    equilibrium_du(cfg->equilibrium, u, du);
+    omegas(cfg, &wp, &wm);
+    /* d feq_q / d f_p = w_q d rho/d f_p + sum_i d feq_q/d u_i d u_i/d f_p,
+     * with d rho / d f_p = 1 and d u_i / d f_p = c_pi (rho0 = 1). */
+    for (int q = 0; q < Q; ++q)
+        for (int p = 0; p < Q; ++p)
+            dfeq[q][p] = W[q] + du[q][0] * C[p][0] + du[q][1] * C[p][1] + du[q][2] * C[p][2];
+    for (int q = 0; q < Q; ++q) {
+        int o = OPP[q];
+        double F = 3.0 * W[q] * (C[q][0] * cfg->accel[0] + C[q][1] * cfg->accel[1] + C[q][2] * cfg->accel[2]);
+        for (int p = 0; p < Q; ++p) {
+            double dqp = (q == p) ? 1.0 : 0.0, dop = (o == p) ? 1.0 : 0.0;
+            double dfp = 0.5 * (dqp + dop), dfm = 0.5 * (dqp - dop);
+            double dep = 0.5 * (dfeq[q][p] + dfeq[o][p]), dem = 0.5 * (dfeq[q][p] - dfeq[o][p]);
+            J[q][p] = dqp - wp * (dfp - dep) - wm * (dfm - dem);
+        }
+        dfs_dwp[q] = -(0.5 * (f[q] + f[o]) - 0.5 * (feq[q] + feq[o]));
+        dfs_dwm[q] = -(0.5 * (f[q] - f[o]) - 0.5 * (feq[q] - feq[o])) - 0.5 * F;
+    }
+}
+
+/* lam_t = (d state(t+1) / d state(t))^T lam_next, and the contributions of
+ * this step to dL/d omega+ and dL/d omega- (added to grad_omega[0..1]).
+ * For SRT both omegas are 1/tau and dL/d omega = grad_omega[0] + grad_omega[1]. */
+int oracle_adjoint_step(const oracle_cfg *cfg, const double *f_t, const double *lam_next,
+                        double *lam_t, double *grad_omega)
+{
+    build_lattice();
+    if (cfg->rho0_is_rho) return 1;
+    double gp = 0.0, gm = 0.0;
+    for (int z = 0; z < cfg->nz; ++z)
+        for (int y = 0; y < cfg->ny; ++y)
+            for (int x = 0; x < cfg->nx; ++x) {
+                long k = cell_index(cfg, x, y, z);
+                double J[Q][Q], dwp[Q], dwm[Q], mu[Q];
+                collide_jacobian(cfg, f_t + k * Q, J, dwp, dwm);
+                /* transpose of the push: fs_q(x) went to f_q(x + c_q) or,
+                 * through a wall, to f_qbar(x). */
+                for (int q = 0; q < Q; ++q) {
+                    long t;
+                    if (link_target(cfg, x, y, z, q, &t))
+                        mu[q] = lam_next[k * Q + OPP[q]];
+                    else
+                        mu[q] = lam_next[t * Q + q];
+                }
+                for (int p = 0; p < Q; ++p) {
+                    double s = 0.0;
+                    for (int q = 0; q < Q; ++q) s += mu[q] * J[q][p];
+                    lam_t[k * Q + p] = s;
+                }
+                for (int q = 0; q < Q; ++q) {
+                    gp += mu[q] * dwp[q];
+                    gm += mu[q] * dwm[q];
+                }
+            }
+    grad_omega[0] += gp;
+    grad_omega[1] += gm;
+    return 0;
+}
+
+/* dL/df_q(T) for L = 1/2 sum_x |u(x,T) - u_target(x)|^2 (rho0 = 1):
+ * lam_q = sum_i (u_i - target_i) c_qi.  Returns L in *loss. */
+int oracle_loss_velocity_l2(const oracle_cfg *cfg, const double *f, const double *u_target,
+                            double *lam, double *loss)
+{
+    build_lattice();
+    if (cfg->rho0_is_rho) return 1;
+    long n = (long)cfg->nx * cfg->ny * cfg->nz;
+    double L = 0.0;
+    for (long k = 0; k < n; ++k) {
+        double r, r0, u[3], g[3];
+        cell_moments(cfg, f + k * Q, &r, &r0, u);
+        for (int i = 0; i < 3; ++i) {
+            g[i] = u[i] - u_target[i * n + k];
+            L += 0.5 * g[i] * g[i];
+        }
+        for (int q = 0; q < Q; ++q)
+            lam[k * Q + q] = g[0] * C[q][0] + g[1] * C[q][1] + g[2] * C[q][2];
+    }
+    *loss = L;
+    return 0;
+}
+
+/* dL/du0_i(x) = sum_q lam0_q(x) d feq_q / d u_i (rho(x), u0(x)), from
+ * f(0) = feq(rho, u0). */
+int oracle_adjoint_init_velocity(const oracle_cfg *cfg, const double *u0, const double *lam0,
+                                 double *grad_u0)
+{
+    build_lattice();
+    if (cfg->rho0_is_rho) return 1;
+    long n = (long)cfg->nx * cfg->ny * cfg->nz;
+    for (long k = 0; k < n; ++k) {
+        double uk[3] = {u0[k], u0[n + k], u0[2 * n + k]}, d[Q][3];
+        equilibrium_du(cfg->equilibrium, uk, d);
+        for (int i = 0; i < 3; ++i) {
+            double s = 0.0;
+            for (int q = 0; q < Q; ++q) s += lam0[k * Q + q] * d[q][i];
+            grad_u0[i * n + k] = s;
+        }
+    }
+    return 0;
+}
+
+/* d omega+/d tau and d omega-/d tau for the configured collision. */
+void oracle_domega_dtau(const oracle_cfg *cfg, double *dwp, double *dwm)
+{
+    double tau = cfg->tau;
+    *dwp = -1.0 / (tau * tau);
+    if (cfg->collision == 1) {
+        double tm = 0.5 + cfg->trt_magic / (tau - 0.5);
+        double dtm = -cfg->trt_magic / ((tau - 0.5) * (tau - 0.5));
+        *dwm = -dtm / (tm * tm);
+    } else {
+        *dwm = *dwp;
+    }
+}
