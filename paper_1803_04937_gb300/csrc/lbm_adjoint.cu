@@ -1,0 +1,280 @@
+// Reverse-mode adjoint of the D3Q19 step (rho0 = 1).
+//
+// Forward map of one step: state(t+1) = S(C(state(t))), C the collision of
+// Eq. 15 (or its TRT split) per cell, S the streaming permutation with
+// half-way bounce-back.  The adjoint applies S^T (a gather from x + c_q, or
+// from the opposite slot through a wall) and then C^T per cell.  With
+// mu = S^T lambda(t+1), mu+/- the symmetric / antisymmetric parts over
+// opposite pairs and nu = omega+ mu+ + omega- mu-, the transposed Jacobian of
+// the collision is
+//     lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + sum_q nu_q dfeq_q/df_p,
+//     dfeq_q/df_p = w_q + c_p . dfeq_q/du     (d rho/d f_p = 1, d u/d f_p = c_p),
+// so lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G with
+// A = sum_q w_q nu_q and G = sum_q nu_q dfeq_q/du.  For feq = D3Q19-S +
+// kappa * Delta (see lbm_device.cuh),
+//     sum_q nu_q dfeq^S_q/du = 3 B + 9 Cm u - 3 A u,
+// B = sum_q w_q nu_q c_q, Cm = sum_q w_q nu_q c_q c_q^T, and the Delta part
+// adds, per component i, nu_0 u_i / 3 - (u_i / 6)(sum of the face-pair sums
+// on the two other axes) + (u_i / 12)(sum of nu over the edges normal to i).
+// The step's derivatives with respect to omega+ and omega- are
+//     dL/domega+ = -sum_q mu+_q (f_q - feq_q),
+//     dL/domega- = -sum_q mu-_q (f_q - feq_q) - 1/2 sum_q mu_q F_q.
+#include "lbm_device.cuh"
+#include "lbm_launch.h"
+
+namespace lbm {
+
+static dim3 adj_block() { return dim3(128, 2, 1); }
+static dim3 adj_grid(const Geo &g) { return dim3((g.nx + 127) / 128, (g.ny + 1) / 2, g.nz); }
+int adjoint_blocks(const Geo &g)
+{
+    dim3 gr = adj_grid(g);
+    return (int)(gr.x * gr.y * gr.z);
+}
+
+// G = sum_q nu_q dfeq_q/du and A = sum_q w_q nu_q at velocity u.
+template <typename R>
+__device__ __forceinline__ void contract_dfeq_du(const R nu[Q], const R u[3], R kappa, R G[3], R &A)
+{
+    R a = WQ<R>(0) * nu[0];
+    R b[3] = {R(0), R(0), R(0)};
+    R cxx = R(0), cyy = R(0), czz = R(0), cxy = R(0), cxz = R(0), cyz = R(0);
+    R face[3] = {R(0), R(0), R(0)};  // nu summed over the two faces of each axis
+    R edge[3] = {R(0), R(0), R(0)};  // nu summed over the four edges normal to each axis
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const R w = WQ<R>(q);
+        const R wn = w * nu[q];
+        a += wn;
+        if (CX(q)) b[0] += R(CX(q)) * wn;
+        if (CY(q)) b[1] += R(CY(q)) * wn;
+        if (CZ(q)) b[2] += R(CZ(q)) * wn;
+        if (CX(q)) cxx += wn;
+        if (CY(q)) cyy += wn;
+        if (CZ(q)) czz += wn;
+        if (CX(q) * CY(q)) cxy += R(CX(q) * CY(q)) * wn;
+        if (CX(q) * CZ(q)) cxz += R(CX(q) * CZ(q)) * wn;
+        if (CY(q) * CZ(q)) cyz += R(CY(q) * CZ(q)) * wn;
+        if (NORM2(q) == 1) {
+            face[CX(q) ? 0 : (CY(q) ? 1 : 2)] += nu[q];
+        } else {
+            edge[CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2)] += nu[q];
+        }
+    }
+    const R cu[3] = {cxx * u[0] + cxy * u[1] + cxz * u[2], cxy * u[0] + cyy * u[1] + cyz * u[2],
+                     cxz * u[0] + cyz * u[1] + czz * u[2]};
+    const R fs = face[0] + face[1] + face[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R gs = R(3) * b[i] + R(9) * cu[i] - R(3) * a * u[i];
+        R gd = nu[0] * u[i] * (R(1) / R(3)) - u[i] * (fs - face[i]) * (R(1) / R(6)) + u[i] * edge[i] * (R(1) / R(12));
+        G[i] = gs + kappa * gd;
+    }
+    A = a;
+}
+
+template <typename L>
+__global__ void k_adjoint_seed(const void *grad_rho, const void *grad_u, int dtype, L *lam, Geo g)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+    double gu[3], gr = 0.0;
+    for (int i = 0; i < 3; ++i)
+        gu[i] = dtype == 0 ? ((const double *)grad_u)[i * g.ncell + cell] : ((const float *)grad_u)[i * g.ncell + cell];
+    if (grad_rho) gr = dtype == 0 ? ((const double *)grad_rho)[cell] : ((const float *)grad_rho)[cell];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        lam[(long long)q * g.ncell + cell] = L(CX(q) * gu[0] + CY(q) * gu[1] + CZ(q) * gu[2] + gr);
+}
+
+template <typename T, typename L>
+__global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ state, const L *__restrict__ lam_next,
+                                                      L *__restrict__ lam, double *partial, Geo g,
+                                                      Coll<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    __shared__ double sh[32];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    double gp_acc = 0.0, gm_acc = 0.0;
+    if (x < g.nx && y < g.ny) {
+        Cell c(x, y, z, g);
+        const int self = c.self();
+        R f[Q];
+        gather<AB>(state, c, g.ncell, f);
+        R drho, rho0, u[3];
+        macro(f, p, drho, rho0, u);
+        const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        // S^T: the value that left x along c_q arrived at x + c_q (or, through
+        // a wall, at the opposite slot of x).
+        R mu[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            bool wall;
+            int dst = c.template along<1>(q, wall);
+            long long off = wall ? (long long)OPP(q) * g.ncell + self : (long long)q * g.ncell + dst;
+            mu[q] = R(lam_next[off]);
+        }
+        // omega gradients (per cell), and nu
+        R nu[Q];
+        R eq0 = rest_equilibrium(uu, drho, rho0, p.kappa);
+        R cgp = mu[0] * (f[0] - eq0);
+        R cgm = R(0);
+        nu[0] = p.omega_p * mu[0];
+        R fa = R(0);  // sum_q mu_q F_q / 3, F_q = 3 w_q c_q . a
+#define LBM_ADJ_PAIR(k)                                                                    \
+    {                                                                                      \
+        constexpr int q = 2 * k + 1;                                                       \
+        R sym, asym;                                                                       \
+        pair_equilibrium<R, q>(u, uu, drho, rho0, p.kappa, sym, asym);                     \
+        R mp = R(0.5) * (mu[q] + mu[q + 1]);                                               \
+        R mm = R(0.5) * (mu[q] - mu[q + 1]);                                               \
+        cgp += mp * (f[q] + f[q + 1] - R(2) * sym);                                         \
+        cgm += mm * (f[q] - f[q + 1] - R(2) * asym);                                        \
+        fa += (mu[q] - mu[q + 1]) * WQ<R>(q) *                                             \
+              R(2) * (R(CX(q)) * p.half_a[0] + R(CY(q)) * p.half_a[1] + R(CZ(q)) * p.half_a[2]); \
+        nu[q] = p.omega_p * mp + p.omega_m * mm;                                           \
+        nu[q + 1] = p.omega_p * mp - p.omega_m * mm;                                       \
+    }
+        LBM_ADJ_PAIR(0) LBM_ADJ_PAIR(1) LBM_ADJ_PAIR(2) LBM_ADJ_PAIR(3) LBM_ADJ_PAIR(4)
+        LBM_ADJ_PAIR(5) LBM_ADJ_PAIR(6) LBM_ADJ_PAIR(7) LBM_ADJ_PAIR(8)
+#undef LBM_ADJ_PAIR
+        gp_acc = -(double)cgp;
+        gm_acc = -(double)cgm - 0.5 * 3.0 * (double)fa;
+        R G[3], A;
+        contract_dfeq_du(nu, u, p.kappa, G, A);
+        lam[self] = L(mu[0] - p.omega_p * mu[0] + A);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            R mp = R(0.5) * (mu[q] + mu[q + 1]);
+            R mm = R(0.5) * (mu[q] - mu[q + 1]);
+            R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
+            lam[(long long)q * g.ncell + self] = L(mu[q] - p.omega_p * mp - p.omega_m * mm + A + cg);
+            lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] - p.omega_p * mp + p.omega_m * mm + A - cg);
+        }
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    // block_sum expects a 1D thread index; fold the 2D block into it.
+    double s0 = gp_acc, s1 = gm_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    }
+    const int lane = tid & 31, warp = tid >> 5, nwarp = (blockDim.x * blockDim.y) >> 5;
+    if (lane == 0) {
+        sh[warp] = s0;
+        sh[16 + warp] = s1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int w = 0; w < nwarp; ++w) {
+            a0 += sh[w];
+            a1 += sh[16 + w];
+        }
+        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partial[2 * b] = a0;
+        partial[2 * b + 1] = a1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adjoint_final(const double *partial, long long nblocks, double *grad_omega)
+{
+    __shared__ double sh[32];
+    double a0 = 0.0, a1 = 0.0;
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        a0 += partial[2 * b];
+        a1 += partial[2 * b + 1];
+    }
+    a0 = block_sum(a0, sh);
+    a1 = block_sum(a1, sh);
+    if (threadIdx.x == 0) {
+        grad_omega[0] += a0;
+        grad_omega[1] += a1;
+    }
+}
+
+template <typename In, typename L, typename R>
+__global__ void k_adjoint_init_velocity(const In *u0, const L *lam0, In *grad_u0, Geo g, R kappa)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+    R u[3] = {R(u0[cell]), R(u0[g.ncell + cell]), R(u0[2 * g.ncell + cell])};
+    R nu[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) nu[q] = R(lam0[(long long)q * g.ncell + cell]);
+    R G[3], A;
+    contract_dfeq_du(nu, u, kappa, G, A);
+    for (int i = 0; i < 3; ++i) grad_u0[i * g.ncell + cell] = In(G[i]);
+}
+
+// ---------------------------------------------------------------- dispatch
+
+cudaError_t launch_adjoint_seed(int prec, const void *grad_rho, const void *grad_u, int dtype, void *lambda,
+                                const Geo &g, cudaStream_t s)
+{
+    if (prec == P_F64)
+        k_adjoint_seed<double><<<adj_grid(g), adj_block(), 0, s>>>(grad_rho, grad_u, dtype, (double *)lambda, g);
+    else
+        k_adjoint_seed<float><<<adj_grid(g), adj_block(), 0, s>>>(grad_rho, grad_u, dtype, (float *)lambda, g);
+    return cudaGetLastError();
+}
+
+template <typename T, typename L>
+static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam, double *grad_omega, double *scratch,
+                              const Geo &g, const CollBoth &cb, cudaStream_t s)
+{
+    using R = typename Storage<T>::R;
+    Coll<R> p = to_coll<R>(cb);
+    k_adjoint_step<T, L><<<adj_grid(g), adj_block(), 0, s>>>((const T *)state, (const L *)lam_next, (L *)lam,
+                                                              scratch, g, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adjoint_final<<<1, 256, 0, s>>>(scratch, (long long)adjoint_blocks(g), grad_omega);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step(int prec, const void *state, const void *lam_next, void *lam, double *grad_omega,
+                                double *scratch, const Geo &g, const CollBoth &c, cudaStream_t s)
+{
+    switch (prec) {
+    case P_F64: return adj_step_t<double, double>(state, lam_next, lam, grad_omega, scratch, g, c, s);
+    case P_F32: return adj_step_t<float, float>(state, lam_next, lam, grad_omega, scratch, g, c, s);
+    case P_F16: return adj_step_t<__half, float>(state, lam_next, lam, grad_omega, scratch, g, c, s);
+    case P_BF16: return adj_step_t<__nv_bfloat16, float>(state, lam_next, lam, grad_omega, scratch, g, c, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint_init_velocity(int prec, const void *rho, const void *u0, int dtype, const void *lam0,
+                                         void *grad_u0, const Geo &g, const CollBoth &c, cudaStream_t s)
+{
+    (void)rho;  // with rho0 = 1, dfeq/du does not depend on rho
+    if (prec == P_F64) {
+        if (dtype == 0)
+            k_adjoint_init_velocity<double, double, double><<<adj_grid(g), adj_block(), 0, s>>>(
+                (const double *)u0, (const double *)lam0, (double *)grad_u0, g, c.kappa);
+        else
+            k_adjoint_init_velocity<float, double, double><<<adj_grid(g), adj_block(), 0, s>>>(
+                (const float *)u0, (const double *)lam0, (float *)grad_u0, g, c.kappa);
+    } else {
+        if (dtype == 0)
+            k_adjoint_init_velocity<double, float, float><<<adj_grid(g), adj_block(), 0, s>>>(
+                (const double *)u0, (const float *)lam0, (double *)grad_u0, g, (float)c.kappa);
+        else
+            k_adjoint_init_velocity<float, float, float><<<adj_grid(g), adj_block(), 0, s>>>(
+                (const float *)u0, (const float *)lam0, (float *)grad_u0, g, (float)c.kappa);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

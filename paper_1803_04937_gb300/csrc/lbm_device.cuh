@@ -1,0 +1,364 @@
+// Device-side building blocks of the D3Q19 library: the lattice, storage
+// conversions, lattice geometry (periodic wrap and half-way bounce-back), the
+// gather / scatter patterns of the A/B and AA propagation schemes, and the
+// collision of Eq. 15 (SRT) or its TRT split, written in shifted variables
+// g_q = f_q - w_q.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_launch.h"
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// D3Q19 velocity set of Sec. 2.3 in this library's order: q = 0 rest, then
+// nine pairs (q, q+1) with c_{q+1} = -c_q: three faces, six edges.
+__host__ __device__ constexpr int CX(int q)
+{
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[q];
+}
+__host__ __device__ constexpr int CY(int q)
+{
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[q];
+}
+__host__ __device__ constexpr int CZ(int q)
+{
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[q];
+}
+__host__ __device__ constexpr int OPP(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr int NORM2(int q) { return CX(q) * CX(q) + CY(q) * CY(q) + CZ(q) * CZ(q); }
+// weights 1/3, 1/18, 1/36 (Sec. 2.3)
+template <typename R>
+__host__ __device__ constexpr R WQ(int q)
+{
+    return NORM2(q) == 0 ? R(1) / R(3) : (NORM2(q) == 1 ? R(1) / R(18) : R(1) / R(36));
+}
+
+// ---------------------------------------------------------------- storage
+
+template <typename T> struct Storage;
+template <> struct Storage<double> {
+    using R = double;
+    static __device__ __forceinline__ R load(const double *p) { return *p; }
+    static __device__ __forceinline__ void store(double *p, R v) { *p = v; }
+};
+template <> struct Storage<float> {
+    using R = float;
+    static __device__ __forceinline__ R load(const float *p) { return *p; }
+    static __device__ __forceinline__ void store(float *p, R v) { *p = v; }
+};
+template <> struct Storage<__half> {
+    using R = float;
+    static __device__ __forceinline__ R load(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void store(__half *p, R v) { *p = __float2half_rn(v); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ R load(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, R v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------- geometry
+
+struct Geo {
+    int nx, ny, nz;
+    int wall_x, wall_y, wall_z;  // 1: half-way bounce-back walls at both ends
+    long long ncell;             // plane stride of the SoA grid, nx * ny * nz
+};
+
+// One lattice cell with its wrapped neighbour coordinates and the wall flags
+// of its six faces (true when the neighbour across that face is beyond a wall).
+struct Cell {
+    int x, y, z;
+    int xm, xp, ym, yp, zm, zp;
+    bool bxm, bxp, bym, byp, bzm, bzp;
+    int nx, nxy;
+
+    __device__ __forceinline__ Cell(int x_, int y_, int z_, const Geo &g) : x(x_), y(y_), z(z_)
+    {
+        xm = x == 0 ? g.nx - 1 : x - 1;
+        xp = x == g.nx - 1 ? 0 : x + 1;
+        ym = y == 0 ? g.ny - 1 : y - 1;
+        yp = y == g.ny - 1 ? 0 : y + 1;
+        zm = z == 0 ? g.nz - 1 : z - 1;
+        zp = z == g.nz - 1 ? 0 : z + 1;
+        bxm = g.wall_x && x == 0;
+        bxp = g.wall_x && x == g.nx - 1;
+        bym = g.wall_y && y == 0;
+        byp = g.wall_y && y == g.ny - 1;
+        bzm = g.wall_z && z == 0;
+        bzp = g.wall_z && z == g.nz - 1;
+        nx = g.nx;
+        nxy = g.nx * g.ny;
+    }
+    __device__ __forceinline__ int self() const { return (z * nxy) + y * nx + x; }
+
+    // Cell x + s*c_q (s = +1: push target, s = -1: pull source).  Sets
+    // `wall` when the link crosses a bounce-back wall.
+    template <int S>
+    __device__ __forceinline__ int along(int q, bool &wall) const
+    {
+        const int cx = S * CX(q), cy = S * CY(q), cz = S * CZ(q);
+        int xs = cx == 0 ? x : (cx > 0 ? xp : xm);
+        int ys = cy == 0 ? y : (cy > 0 ? yp : ym);
+        int zs = cz == 0 ? z : (cz > 0 ? zp : zm);
+        bool w = false;
+        if (cx > 0) w |= bxp;
+        if (cx < 0) w |= bxm;
+        if (cy > 0) w |= byp;
+        if (cy < 0) w |= bym;
+        if (cz > 0) w |= bzp;
+        if (cz < 0) w |= bzm;
+        wall = w;
+        return zs * nxy + ys * nx + xs;
+    }
+};
+
+// State layouts.  The canonical state is f_q(x, t) after streaming, before
+// collision.  How it sits in memory:
+//   AB      : grid[q][x - c_q] (the previous step's post-collision value that
+//             streams into x); through a wall, grid[qbar][x].
+//   AA_EVEN : grid[q][x] (after an even number of AA steps).
+//   AA_ODD  : grid[qbar][x - c_q]; through a wall grid[q][x] (after an odd
+//             number of AA steps).
+enum Layout { AB = 0, AA_EVEN = 1, AA_ODD = 2 };
+
+template <int L, typename T, typename R>
+__device__ __forceinline__ void gather(const T *grid, const Cell &c, long long ncell, R g[Q])
+{
+    const int self = c.self();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long off;
+        if (L == AA_EVEN) {
+            off = (long long)q * ncell + self;
+        } else {
+            bool wall;
+            int src = c.template along<-1>(q, wall);
+            if (L == AB)
+                off = wall ? (long long)OPP(q) * ncell + self : (long long)q * ncell + src;
+            else
+                off = wall ? (long long)q * ncell + self : (long long)OPP(q) * ncell + src;
+        }
+        g[q] = Storage<T>::load(grid + off);
+    }
+}
+
+// Where post-collision values of a step go:
+//   AB_NEXT : grid[q][x]                 (pull scheme, next step gathers them)
+//   AA_EVEN : grid[qbar][x]
+//   AA_ODD  : grid[q][x + c_q]; through a wall grid[qbar][x]
+// and, to write a canonical state f_q(x) into a grid so that the AB gather
+// returns it: AB_CANON : grid[q][x - c_q]; through a wall grid[qbar][x].
+enum Dest { D_AB_NEXT = 0, D_AA_EVEN = 1, D_AA_ODD = 2, D_AB_CANON = 3 };
+
+template <int D, typename T, typename R>
+__device__ __forceinline__ void scatter(T *grid, const Cell &c, long long ncell, const R g[Q])
+{
+    const int self = c.self();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long off;
+        if (D == D_AB_NEXT) {
+            off = (long long)q * ncell + self;
+        } else if (D == D_AA_EVEN) {
+            off = (long long)OPP(q) * ncell + self;
+        } else if (D == D_AA_ODD) {
+            bool wall;
+            int dst = c.template along<1>(q, wall);
+            off = wall ? (long long)OPP(q) * ncell + self : (long long)q * ncell + dst;
+        } else {
+            bool wall;
+            int dst = c.template along<-1>(q, wall);
+            off = wall ? (long long)OPP(q) * ncell + self : (long long)q * ncell + dst;
+        }
+        Storage<T>::store(grid + off, g[q]);
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+
+// Sum over the block (blockDim.x a multiple of 32, at most 1024 threads);
+// the result is valid in thread 0.  Fixed order: deterministic.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    v = 0.0;
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double block_max(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    v = 0.0;
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- physics
+
+// Per-launch collision constants (prepared on the host).
+template <typename R>
+struct Coll {
+    R omega_p;        // 1 / tau
+    R omega_m;        // 1 / tau-  (= omega_p for SRT)
+    R kappa;          // 0: D3Q19-S (Eq. 14), 1: D3Q19-I (Eq. 22)
+    R half_a[3];      // a / 2, the velocity shift of Eq. 17
+    R force[9];       // (1 - omega_m / 2) F_q for the first member q = 2k+1 of pair k
+    int rho0_is_rho;  // 0: rho0 = 1, 1: rho0 = rho
+};
+
+// Macroscopic quantities of the shifted populations: drho = rho - 1,
+// u from rho0 u = j + a/2 (Eq. 16, Eq. 17), and rho0.
+template <typename R>
+static inline Coll<R> to_coll(const CollBoth &c)
+{
+    Coll<R> p;
+    p.omega_p = R(c.omega_p);
+    p.omega_m = R(c.omega_m);
+    p.kappa = R(c.kappa);
+    for (int i = 0; i < 3; ++i) p.half_a[i] = R(c.half_a[i]);
+    for (int k = 0; k < 9; ++k) p.force[k] = R(c.force[k]);
+    p.rho0_is_rho = c.rho0_is_rho;
+    return p;
+}
+
+template <typename R>
+__device__ __forceinline__ void macro(const R g[Q], const Coll<R> &p, R &drho, R &rho0, R u[3])
+{
+    R s = g[0];
+    R jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        s += g[q];
+        if (CX(q) > 0) jx += g[q];
+        if (CX(q) < 0) jx -= g[q];
+        if (CY(q) > 0) jy += g[q];
+        if (CY(q) < 0) jy -= g[q];
+        if (CZ(q) > 0) jz += g[q];
+        if (CZ(q) < 0) jz -= g[q];
+    }
+    drho = s;
+    rho0 = p.rho0_is_rho ? R(1) + s : R(1);
+    R inv = p.rho0_is_rho ? R(1) / rho0 : R(1);
+    u[0] = (jx + p.half_a[0]) * inv;
+    u[1] = (jy + p.half_a[1]) * inv;
+    u[2] = (jz + p.half_a[2]) * inv;
+}
+
+// Equilibrium of pair k (q = 2k+1 and its opposite) in shifted form:
+//   geq_q = sym + asym,  geq_qbar = sym - asym,
+// with the standard part w (drho + rho0 (9/2 (c.u)^2 - 3/2 u^2)), asym =
+// 3 w rho0 c.u, plus kappa * rho0 * Delta_q where D3Q19-I = D3Q19-S + Delta:
+//   face along axis a:   Delta = -(u^2 - u_a^2) / 12
+//   edge in plane (a,b): Delta = u_c^2 / 24   (c the third axis)
+// (the difference of Eq. 22 and Eq. 14 written per velocity group; both
+// equilibria run the same instructions and differ only in kappa).
+template <typename R, int q>
+__device__ __forceinline__ void pair_equilibrium(const R u[3], R uu, R drho, R rho0, R kappa, R &sym, R &asym)
+{
+    constexpr int cx = CX(q), cy = CY(q), cz = CZ(q);
+    const R w = WQ<R>(q);
+    R cu = R(cx) * u[0] + R(cy) * u[1] + R(cz) * u[2];
+    R delta;
+    if (NORM2(q) == 1) {
+        R ua = cx != 0 ? u[0] : (cy != 0 ? u[1] : u[2]);
+        delta = (ua * ua - uu) * (R(1) / R(12));
+    } else {
+        R uc = cx == 0 ? u[0] : (cy == 0 ? u[1] : u[2]);
+        delta = uc * uc * (R(1) / R(24));
+    }
+    sym = w * (drho + rho0 * (R(4.5) * cu * cu - R(1.5) * uu)) + kappa * rho0 * delta;
+    asym = w * rho0 * R(3) * cu;
+}
+
+template <typename R>
+__device__ __forceinline__ R rest_equilibrium(R uu, R drho, R rho0, R kappa)
+{
+    return WQ<R>(0) * (drho - rho0 * R(1.5) * uu) + kappa * rho0 * uu * (R(1) / R(6));
+}
+
+// Collision in place: g <- g - omega+ (g+ - geq+) - omega- (g- - geq-) +
+// (1 - omega-/2) F_q.  For SRT omega- = omega+ and this is Eq. 15.
+template <typename R, int k>
+__device__ __forceinline__ void collide_pair(R g[Q], const R u[3], R uu, R drho, R rho0, const Coll<R> &p)
+{
+    constexpr int q = 2 * k + 1;
+    R sym, asym;
+    pair_equilibrium<R, q>(u, uu, drho, rho0, p.kappa, sym, asym);
+    R gp = R(0.5) * (g[q] + g[q + 1]);
+    R gm = R(0.5) * (g[q] - g[q + 1]);
+    R a1 = p.omega_p * (gp - sym);
+    R a2 = p.omega_m * (gm - asym);
+    g[q] = g[q] - a1 - a2 + p.force[k];
+    g[q + 1] = g[q + 1] - a1 + a2 - p.force[k];
+}
+
+template <typename R>
+__device__ __forceinline__ void collide(R g[Q], const Coll<R> &p)
+{
+    R drho, rho0, u[3];
+    macro(g, p, drho, rho0, u);
+    R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    g[0] = g[0] - p.omega_p * (g[0] - rest_equilibrium(uu, drho, rho0, p.kappa));
+    collide_pair<R, 0>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 1>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 2>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 3>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 4>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 5>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 6>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 7>(g, u, uu, drho, rho0, p);
+    collide_pair<R, 8>(g, u, uu, drho, rho0, p);
+}
+
+// Shifted equilibrium geq_q = feq_q(rho, u) - w_q for all q (lbm_init).
+template <typename R>
+__device__ __forceinline__ void equilibrium_all(R rho, const R u[3], const Coll<R> &p, R g[Q])
+{
+    R drho = rho - R(1);
+    R rho0 = p.rho0_is_rho ? rho : R(1);
+    R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    g[0] = rest_equilibrium(uu, drho, rho0, p.kappa);
+#define LBM_EQ_PAIR(k)                                                              \
+    {                                                                               \
+        R s_, a_;                                                                   \
+        pair_equilibrium<R, 2 * k + 1>(u, uu, drho, rho0, p.kappa, s_, a_);         \
+        g[2 * k + 1] = s_ + a_;                                                     \
+        g[2 * k + 2] = s_ - a_;                                                     \
+    }
+    LBM_EQ_PAIR(0) LBM_EQ_PAIR(1) LBM_EQ_PAIR(2) LBM_EQ_PAIR(3) LBM_EQ_PAIR(4)
+    LBM_EQ_PAIR(5) LBM_EQ_PAIR(6) LBM_EQ_PAIR(7) LBM_EQ_PAIR(8)
+#undef LBM_EQ_PAIR
+}
+
+}  // namespace lbm

@@ -1,0 +1,197 @@
+"""Python front end of the D3Q19 library: a ``Simulation`` owns torch-allocated
+device buffers and drives the C ABI (include/lbm.h) through ctypes.
+
+Every computation runs in the CUDA kernels of ``liblbm_gb300.so``; this module
+only allocates memory, marshals pointers and checks status codes.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import check
+
+_PRECISION = {"f64": _lib.F64, "f32": _lib.F32, "f16s": _lib.F16S, "bf16s": _lib.BF16S}
+_STORAGE_DTYPE = {_lib.F64: torch.float64, _lib.F32: torch.float32, _lib.F16S: torch.float16,
+                  _lib.BF16S: torch.bfloat16}
+_EQ = {"standard": _lib.EQ_STANDARD, "improved": _lib.EQ_IMPROVED}
+_COLL = {"srt": _lib.SRT, "trt": _lib.TRT}
+_PATTERN = {"ab": _lib.PATTERN_AB, "aa": _lib.PATTERN_AA}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _field_dtype(t):
+    if t.dtype == torch.float64:
+        return _lib.DTYPE_F64
+    if t.dtype == torch.float32:
+        return _lib.DTYPE_F32
+    raise TypeError("macroscopic fields must be float64 or float32, got %s" % t.dtype)
+
+
+def velocity_set():
+    """(c[19,3], w[19], opp[19]) in the library's D3Q19 order."""
+    lib = _lib.load()
+    c = (ctypes.c_int * 57)()
+    w = (ctypes.c_double * 19)()
+    o = (ctypes.c_int * 19)()
+    check(lib.lbm_velocity_set(c, w, o))
+    return (torch.tensor(list(c), dtype=torch.int64).view(19, 3), torch.tensor(list(w), dtype=torch.float64),
+            torch.tensor(list(o), dtype=torch.int64))
+
+
+class Simulation:
+    """One D3Q19 lattice on one GPU.
+
+    Parameters mirror ``lbm_create`` / ``lbm_set_option``: equilibrium
+    ("standard" = Eq. 14, "improved" = Eq. 22), collision ("srt" | "trt"), tau,
+    storage precision ("f64" | "f32" | "f16s" | "bf16s"), TRT magic parameter,
+    body force a, half-way bounce-back walls per axis, rho0 mode and
+    propagation pattern ("ab" | "aa").  Work is enqueued on ``stream`` (default:
+    torch's current stream on ``device``).
+    """
+
+    def __init__(self, nx, ny, nz, equilibrium="improved", collision="srt", tau=0.8, precision="f32",
+                 trt_magic=3.0 / 16.0, force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False,
+                 pattern="ab", device="cuda", stream=None, block=None):
+        self._lib = lib = _lib.load()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("the D3Q19 library runs on CUDA devices only")
+        self.precision = _PRECISION[precision]
+        self.storage_dtype = _STORAGE_DTYPE[self.precision]
+        h = ctypes.c_void_p()
+        check(lib.lbm_create(self.nx, self.ny, self.nz, _lib.LBM_D3Q19, _EQ[equilibrium], _COLL[collision],
+                             float(tau), self.precision, ctypes.byref(h)))
+        self._h = h
+        self._set(_lib.OPT_TRT_MAGIC, trt_magic)
+        for i in range(3):
+            self._set(_lib.OPT_FORCE_X + i, force[i])
+            self._set(_lib.OPT_WALLS_X + i, 1.0 if walls[i] else 0.0)
+        self._set(_lib.OPT_RHO0_MODE, 1.0 if rho0_is_rho else 0.0)
+        self._set(_lib.OPT_PATTERN, _PATTERN[pattern])
+        if block is not None:
+            self._set(_lib.OPT_BLOCK_X, block[0])
+            self._set(_lib.OPT_BLOCK_Y, block[1])
+        self.pattern = pattern
+        pdf_bytes = ctypes.c_size_t()
+        ngrids = ctypes.c_int()
+        scratch_bytes = ctypes.c_size_t()
+        check(lib.lbm_required_bytes(h, ctypes.byref(pdf_bytes), ctypes.byref(ngrids), ctypes.byref(scratch_bytes)), h)
+        self.pdf_bytes = pdf_bytes.value
+        shape = (19, self.nz, self.ny, self.nx)
+        self.grids = [torch.empty(shape, dtype=self.storage_dtype, device=self.device) for _ in range(ngrids.value)]
+        self.scratch = torch.zeros(scratch_bytes.value // 8, dtype=torch.float64, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._bind(self.grids[0], self.grids[1] if len(self.grids) > 1 else None)
+
+    # -- low level ---------------------------------------------------------
+    def _set(self, key, value):
+        check(self._lib.lbm_set_option(self._h, key, float(value)), self._h)
+
+    def _bind(self, a, b=None):
+        check(self._lib.lbm_bind(self._h, _ptr(a), _ptr(b), _ptr(self.scratch),
+                                 ctypes.c_void_p(self.stream.cuda_stream)), self._h)
+
+    def option(self, key):
+        v = ctypes.c_double()
+        check(self._lib.lbm_get_option(self._h, key, ctypes.byref(v)), self._h)
+        return v.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny * self.nz
+
+    # -- state -------------------------------------------------------------
+    def init(self, rho, u):
+        """f = feq(rho, u) (Eq. 14 or Eq. 22); rho[nz,ny,nx] (or None) and u[3,nz,ny,nx]."""
+        u = u.to(self.device).contiguous()
+        dt = _field_dtype(u)
+        if rho is not None:
+            rho = rho.to(device=self.device, dtype=u.dtype).contiguous()
+        self._keep = (rho, u)  # kept alive until the kernel has run
+        check(self._lib.lbm_init(self._h, _ptr(rho), _ptr(u), dt), self._h)
+
+    def step(self, n=1):
+        check(self._lib.lbm_step(self._h, int(n)), self._h)
+
+    def moments(self, dtype=torch.float64):
+        """(rho[nz,ny,nx], u[3,nz,ny,nx]) of the current state (Eq. 16, Eq. 17)."""
+        rho = torch.empty(self.shape, dtype=dtype, device=self.device)
+        u = torch.empty((3,) + self.shape, dtype=dtype, device=self.device)
+        self.moments_into(rho, u)
+        return rho, u
+
+    def moments_into(self, rho, u):
+        dt = _field_dtype(u if u is not None else rho)
+        check(self._lib.lbm_moments(self._h, _ptr(rho), _ptr(u), dt), self._h)
+
+    def reduce(self):
+        """FP64 global mass, energy, momentum, max |u| and non-finite count (synchronises)."""
+        out = (ctypes.c_double * _lib.RED_COUNT)()
+        s = self._lib.lbm_reduce(self._h, out)
+        if s not in (_lib.LBM_OK, _lib.LBM_ENONFINITE):
+            check(s, self._h)
+        return {"mass": out[0], "energy": out[1], "momentum": (out[2], out[3], out[4]), "umax": out[5],
+                "nonfinite": int(out[6]), "status": s}
+
+    def steps_done(self):
+        t = ctypes.c_longlong()
+        check(self._lib.lbm_steps_done(self._h, ctypes.byref(t)), self._h)
+        return t.value
+
+    def get_pdfs(self):
+        """Canonical copy f_q - w_q as [19, nz, ny, nx] in storage precision."""
+        out = torch.empty((19,) + self.shape, dtype=self.storage_dtype, device=self.device)
+        check(self._lib.lbm_get_pdfs(self._h, _ptr(out)), self._h)
+        return out
+
+    def set_pdfs(self, pdfs):
+        pdfs = pdfs.to(device=self.device, dtype=self.storage_dtype).contiguous()
+        self._keep = (pdfs,)
+        check(self._lib.lbm_set_pdfs(self._h, _ptr(pdfs)), self._h)
+
+    # -- end to end from host memory -----------------------------------------
+    def run_host(self, rho_host, u_host, nsteps, out=None):
+        """End-to-end call from host memory: copies rho, u (pinned host tensors)
+        to the device, initialises, runs nsteps, and copies rho, u back into
+        ``out`` (pinned host tensors) or new host tensors.  Returns (rho, u)."""
+        s = self.stream
+        with torch.cuda.stream(s):
+            u = u_host.to(self.device, non_blocking=True)
+            rho = rho_host.to(self.device, non_blocking=True) if rho_host is not None else None
+            dt = _field_dtype(u)
+            check(self._lib.lbm_init(self._h, _ptr(rho), _ptr(u), dt), self._h)
+            check(self._lib.lbm_step(self._h, int(nsteps)), self._h)
+            rd = torch.empty(self.shape, dtype=u.dtype, device=self.device)
+            ud = torch.empty_like(u)
+            check(self._lib.lbm_moments(self._h, _ptr(rd), _ptr(ud), dt), self._h)
+            if out is None:
+                out = (torch.empty(rd.shape, dtype=rd.dtype, pin_memory=True),
+                       torch.empty(ud.shape, dtype=ud.dtype, pin_memory=True))
+            out[0].copy_(rd, non_blocking=True)
+            out[1].copy_(ud, non_blocking=True)
+        s.synchronize()
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lbm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,161 @@
+"""Parity of the CUDA time step with the FP64 oracle, element by element, on
+small seeded lattices that span several thread blocks and a ragged tail.
+
+Tolerances (max-norm relative error of u, and absolute error of the
+populations): FP64 storage 1e-12, FP32 storage 1e-5 after the run's steps."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._helpers import gpu_pdfs_in_oracle_layout, oracle_config, random_fields, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+PDF_TOL = {"f64": 1e-13, "f32": 1e-6}
+
+CASES = [
+    dict(equilibrium="improved", collision="srt", tau=0.8),
+    dict(equilibrium="standard", collision="srt", tau=0.55),
+    dict(equilibrium="improved", collision="trt", tau=0.6, force=(2e-4, -1e-4, 5e-5)),
+    dict(equilibrium="standard", collision="trt", tau=0.9, walls=(False, True, False), force=(1e-4, 0, 0)),
+    dict(equilibrium="improved", collision="srt", tau=0.7, walls=(True, False, True)),
+    dict(equilibrium="improved", collision="trt", tau=0.51, walls=(True, True, True), force=(0, 1e-4, -2e-4)),
+    dict(equilibrium="standard", collision="srt", tau=1.3, rho0_is_rho=True, force=(1e-4, 2e-4, 0)),
+    dict(equilibrium="improved", collision="trt", tau=0.75, rho0_is_rho=True, walls=(False, True, False)),
+]
+
+
+def _run_gpu(shape, rho, u, steps, precision, pattern, case):
+    from paper_1803_04937_gb300.lbm import Simulation
+    nz, ny, nx = shape
+    sim = Simulation(nx, ny, nz, precision=precision, pattern=pattern, **case)
+    sim.init(rho.cuda(), u.cuda())
+    sim.step(steps)
+    r, uu = sim.moments(torch.float64)
+    return sim, r.cpu().numpy(), uu.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_step_matches_oracle(case, pattern, precision):
+    kw = CASES[case]
+    shape = (5, 9, 37)  # nz, ny, nx: odd sizes, ragged x blocks
+    rho, u = random_fields(shape, seed=100 + case)
+    steps = 7 if pattern == "aa" else 6  # odd count leaves AA in its odd layout
+    sim, r_g, u_g = _run_gpu(shape, rho, u, steps, precision, pattern, kw)
+    cfg = oracle_config(shape[2], shape[1], shape[0], **kw)
+    f_o = oracle.step(cfg, oracle.init(cfg, rho.numpy(), u.numpy()), steps)
+    r_o, u_o = oracle.moments(cfg, f_o)
+    assert rel_maxnorm(u_g, u_o) < TOL[precision]
+    assert np.abs(r_g - r_o).max() < TOL[precision]
+    f_g = gpu_pdfs_in_oracle_layout(sim)
+    assert np.abs(f_g - f_o).max() < PDF_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s", "f64"])
+@pytest.mark.parametrize("case", [0, 3, 5])
+def test_aa_equals_ab_bitwise(case, precision):
+    """AA and A/B run the same arithmetic per cell: identical bits after any
+    number of steps (also a race check of the in-place pattern)."""
+    kw = CASES[case]
+    shape = (6, 11, 45)
+    rho, u = random_fields(shape, seed=7)
+    for steps in (1, 4, 9):
+        sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw)
+        sb, _, _ = _run_gpu(shape, rho, u, steps, precision, "aa", kw)
+        assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
+        ra, ua = sa.moments(torch.float32)
+        rb, ub = sb.moments(torch.float32)
+        assert torch.equal(ua, ub) and torch.equal(ra, rb)
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_checkpoint_restore_is_bitwise(pattern):
+    from paper_1803_04937_gb300.lbm import Simulation
+    shape = (4, 8, 40)
+    rho, u = random_fields(shape, seed=3)
+    kw = dict(collision="trt", tau=0.6, walls=(False, True, False), force=(1e-4, 0, 0))
+    a = Simulation(40, 8, 4, pattern=pattern, **kw)
+    a.init(rho.cuda(), u.cuda())
+    a.step(5)
+    ck = a.get_pdfs()
+    a.step(6)
+    b = Simulation(40, 8, 4, pattern=pattern, **kw)
+    b.set_pdfs(ck)
+    assert torch.equal(b.get_pdfs(), ck)
+    b.step(6)
+    assert torch.equal(a.get_pdfs(), b.get_pdfs())
+
+
+def test_reductions_match_oracle_and_flag_nonfinite():
+    from paper_1803_04937_gb300.lbm import Simulation
+    shape = (7, 10, 33)
+    rho, u = random_fields(shape, seed=9)
+    kw = dict(equilibrium="improved", collision="srt", tau=0.7, force=(1e-4, -2e-4, 3e-5))
+    sim = Simulation(33, 10, 7, precision="f64", **kw)
+    sim.init(rho.cuda(), u.cuda())
+    sim.step(5)
+    red = sim.reduce()
+    cfg = oracle_config(33, 10, 7, **kw)
+    f = oracle.step(cfg, oracle.init(cfg, rho.numpy(), u.numpy()), 5)
+    r_o, u_o = oracle.moments(cfg, f)
+    c, _, _ = oracle.velocity_set()
+    assert red["mass"] == pytest.approx(f.sum(), rel=1e-14)
+    assert red["energy"] == pytest.approx(0.5 * (u_o ** 2).sum(), rel=1e-12)
+    j = (f.reshape(-1, 19) @ c).sum(axis=0)
+    assert np.allclose(red["momentum"], j, rtol=1e-12, atol=1e-14)
+    assert red["umax"] == pytest.approx(np.sqrt((u_o ** 2).sum(axis=0)).max(), rel=1e-12)
+    assert red["nonfinite"] == 0 and red["status"] == 0
+    # deterministic
+    assert sim.reduce() == red
+    # a NaN planted on the host is reported, not hidden
+    p = sim.get_pdfs()
+    p[3, 2, 4, 5] = float("nan")
+    sim.set_pdfs(p)
+    bad = sim.reduce()
+    assert bad["nonfinite"] == 1 and bad["status"] == 5
+
+
+@pytest.mark.parametrize("precision,bound", [("f16s", 2e-3), ("bf16s", 2e-2)])
+def test_16bit_storage_error_is_bounded(precision, bound):
+    """16-bit shifted storage: velocity error against the FP64 oracle, stated."""
+    shape = (8, 16, 64)
+    rho, u = random_fields(shape, seed=21, amp=0.05, drho=0.0)
+    kw = dict(equilibrium="improved", collision="srt", tau=0.8)
+    _, _, u_g = _run_gpu(shape, rho, u, 20, precision, "ab", kw)
+    cfg = oracle_config(64, 16, 8, **kw)
+    _, u_o = oracle.run(cfg, rho.numpy(), u.numpy(), 20)
+    err = rel_maxnorm(u_g, u_o)
+    print("%s velocity max-norm relative error after 20 steps: %.3e" % (precision, err))
+    assert err < bound
+
+
+def test_tiny_and_degenerate_lattices():
+    """1x1x1 (streaming is the identity), 1-cell-thick slabs in each axis, and
+    walls on a 1-cell axis all agree with the oracle."""
+    for shape, walls in [((1, 1, 1), (False, False, False)), ((1, 1, 7), (False, False, False)),
+                         ((3, 1, 1), (False, False, True)), ((1, 5, 1), (False, True, False)),
+                         ((2, 1, 3), (True, True, False))]:
+        kw = dict(collision="trt", tau=0.7, force=(1e-4, 2e-4, -1e-4), walls=walls)
+        rho, u = random_fields(shape, seed=5)
+        _, _, u_g = _run_gpu(shape, rho, u, 5, "f64", "ab", kw)
+        _, _, u_a = _run_gpu(shape, rho, u, 5, "f64", "aa", kw)
+        cfg = oracle_config(shape[2], shape[1], shape[0], **kw)
+        _, u_o = oracle.run(cfg, rho.numpy(), u.numpy(), 5)
+        assert rel_maxnorm(u_g, u_o) < 1e-12, shape
+        assert rel_maxnorm(u_a, u_o) < 1e-12, shape
+
+
+def test_zero_steps_returns_initial_fields():
+    from paper_1803_04937_gb300.lbm import Simulation
+    shape = (3, 4, 5)
+    rho, u = random_fields(shape, seed=1)
+    for pattern in ("ab", "aa"):
+        sim = Simulation(5, 4, 3, precision="f64", pattern=pattern)
+        sim.init(rho.cuda(), u.cuda())
+        sim.step(0)
+        r, uu = sim.moments()
+        assert torch.allclose(r.cpu(), rho, atol=1e-15) and torch.allclose(uu.cpu(), u, atol=1e-15)
