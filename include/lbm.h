@@ -183,6 +183,29 @@ int lbm_moments(lbm_handle h, void *rho, void *u, int dtype);
  */
 int lbm_reduce(lbm_handle h, double *out);
 
+/*
+ * lbm_reduce without a scratch buffer: the same FP64 reductions of the
+ * current state into host out[LBM_RED_COUNT], for callers that cannot
+ * allocate device memory (for example a host application that hands the
+ * library a fixed memory budget, or code running where cudaMalloc is not
+ * allowed).  The paper has no counterpart; this is an interface convenience.
+ *
+ * Its scratch is a static device array of the library (64 KiB: FP64 partial
+ * sums of up to 1024 reduction blocks, plus the results), held on every GPU
+ * that loads the library until the process exits.  The reduction grid does
+ * not depend on the lattice size, so every lattice lbm_create accepts fits;
+ * should the reduction ever need more rows than the array holds, the call
+ * returns LBM_EUNSUPPORTED with a message.  It calls no allocating routine.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and every call
+ * rewrites the parts it reads, so no clearing is needed, but calls that
+ * overlap on the GPU (other streams, other handles) race on it.  Needs
+ * lbm_bind (grids and stream; the scratch pointer may be NULL).
+ * Synchronises the bound stream.  Returns LBM_ENONFINITE like lbm_reduce.
+ */
+int lbm_reduce_noalloc(lbm_handle h, double *out);
+
 /* Step counter (number of lbm_step time steps since lbm_init / lbm_set_pdfs). */
 int lbm_steps_done(lbm_handle h, long long *t);
 

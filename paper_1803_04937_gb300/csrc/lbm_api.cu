@@ -373,6 +373,27 @@ int lbm_reduce(lbm_handle h, double *out)
     return LBM_OK;
 }
 
+int lbm_reduce_noalloc(lbm_handle h, double *out)
+{
+    int s = check_ready(h);
+    if (s) return s;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
+    if ((long long)lbm::reduce_blocks() * 8 + 8 > lbm::reduce_noalloc_capacity_doubles())
+        return fail(h, LBM_EUNSUPPORTED, "lbm_reduce_noalloc: the reduction needs more partial rows than the "
+                                         "static scratch array holds");
+    double *result = nullptr;
+    cudaError_t e = lbm::launch_reduce_noalloc(h->precision, layout(h), current(h), geo(h), coll(h), h->stream,
+                                               &result);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_reduce_noalloc");
+    e = cudaMemcpyAsync(out, result, LBM_RED_COUNT * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_reduce_noalloc copy");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_reduce_noalloc sync");
+    if (out[LBM_RED_NONFINITE] > 0) return fail(h, LBM_ENONFINITE, "state holds non-finite populations");
+    return LBM_OK;
+}
+
 int lbm_steps_done(lbm_handle h, long long *t)
 {
     if (!h || !t) return LBM_EINVAL;

@@ -47,6 +47,12 @@ int reduce_blocks();
 cudaError_t launch_reduce(int prec, int layout, const void *grid, double *scratch, double *scratch_result,
                           const Geo &g, const CollBoth &c, cudaStream_t stream);
 
+// The same reduction with its scratch in a static device array (lbm_reduce_noalloc);
+// *result receives the device address of the LBM_RED_COUNT results.
+int reduce_noalloc_capacity_doubles();
+cudaError_t launch_reduce_noalloc(int prec, int layout, const void *grid, const Geo &g, const CollBoth &c,
+                                  cudaStream_t s, double **result);
+
 // Adjoint kernels (see lbm.h).
 int adjoint_blocks(const Geo &g);
 cudaError_t launch_adjoint_seed(int prec, const void *grad_rho, const void *grad_u, int dtype, void *lambda,
