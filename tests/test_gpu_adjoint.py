@@ -1,0 +1,120 @@
+"""The GPU adjoint (reverse-mode derivative of the D3Q19 step behind a
+torch.autograd.Function with sqrt(T) checkpointing) against the FP64 CPU
+oracle's adjoint and against central finite differences of the GPU forward."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1803_04937_gb300 import inputs
+from tests._helpers import oracle_config, random_fields, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(equilibrium="improved", collision="srt", tau=0.7),
+    dict(equilibrium="standard", collision="srt", tau=0.9, force=(1e-4, -5e-5, 0.0)),
+    dict(equilibrium="improved", collision="trt", tau=0.62, force=(2e-4, 0.0, 1e-4), walls=(False, True, False)),
+    dict(equilibrium="standard", collision="trt", tau=0.8, walls=(True, False, True)),
+]
+
+
+def _gpu_grad(shape, rho, u0, tgt, steps, precision, case, every=None):
+    from paper_1803_04937_gb300 import adjoint
+    nz, ny, nx = shape
+    dt = torch.float64 if precision == "f64" else torch.float32
+    u = u0.to("cuda", dt).clone().requires_grad_(True)
+    tau = torch.tensor(case["tau"], dtype=torch.float64, requires_grad=True)
+    kw = {k: v for k, v in case.items() if k != "tau"}
+    r, uT = adjoint.simulate(u, tau, steps, nx, ny, nz, rho=rho.to("cuda", dt), precision=precision,
+                             checkpoint_every=every, **kw)
+    L = 0.5 * ((uT.double() - tgt.to("cuda")) ** 2).sum()
+    L.backward()
+    return float(L), u.grad.double().cpu().numpy(), float(tau.grad)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_adjoint_matches_oracle_adjoint(case, precision, tol):
+    kw = CASES[case]
+    shape = (5, 7, 12)
+    rho, u0 = random_fields(shape, seed=40 + case, amp=0.04)
+    _, tgt = random_fields(shape, seed=80 + case, amp=0.04)
+    steps = 10
+    L, gu, gt = _gpu_grad(shape, rho, u0, tgt, steps, precision, kw, every=3)
+    cfg = oracle_config(shape[2], shape[1], shape[0], **kw)
+    Lo, guo, gto = oracle.gradient_velocity_l2(cfg, rho.numpy(), u0.numpy(), tgt.numpy(), steps)
+    assert L == pytest.approx(Lo, rel=max(tol, 1e-12))
+    assert rel_maxnorm(gu, guo) < tol
+    assert gt == pytest.approx(gto, rel=tol)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    kw = CASES[2]
+    shape = (4, 6, 10)
+    rho, u0 = random_fields(shape, seed=5, amp=0.04)
+    _, tgt = random_fields(shape, seed=6, amp=0.04)
+    ref = _gpu_grad(shape, rho, u0, tgt, 13, "f64", kw, every=1)
+    for every in (2, 5, 13, 20):
+        g = _gpu_grad(shape, rho, u0, tgt, 13, "f64", kw, every=every)
+        assert np.array_equal(g[1], ref[1]) and g[2] == ref[2]
+
+
+def test_adjoint_16cube_against_cpu_adjoint():
+    """The 16^3 copy of the adjoint workload (same recipe, |n| <= 7 so 16^3
+    resolves it), T = 400: GPU FP64 adjoint to 1e-10, FP32 adjoint to 1e-3."""
+    n, steps = 16, 400
+    rho, u0 = inputs.random_solenoidal(n, n, n, kmax=7, u_rms=0.02, seed=1)
+    _, tgt = inputs.random_solenoidal(n, n, n, kmax=7, u_rms=0.02, seed=2)
+    case = dict(equilibrium="improved", collision="srt", tau=0.7)
+    cfg = oracle_config(n, n, n, **case)
+    Lo, guo, gto = oracle.gradient_velocity_l2(cfg, rho.numpy(), u0.numpy(), tgt.numpy(), steps)
+    for precision, tol in (("f64", 1e-10), ("f32", 1e-3)):
+        L, gu, gt = _gpu_grad((n, n, n), rho, u0, tgt, steps, precision, case)
+        assert rel_maxnorm(gu, guo) < tol, precision
+        assert gt == pytest.approx(gto, rel=tol), precision
+
+
+def test_adjoint_128cube_against_finite_differences():
+    """Adjoint workload: periodic 128^3, tau = 0.7, D3Q19-I, SRT, T = 400 with
+    sqrt(T) checkpoints, random solenoidal u0 (|n| <= 8, u_rms = 0.02, seed 1),
+    target seed 2.  FP32 adjoint vs central differences of the FP64 GPU forward
+    on 64 random components of u0 (seed 3) and on tau: <= 1e-3 relative."""
+    from paper_1803_04937_gb300 import adjoint
+    n, steps = 128, 400
+    case = dict(equilibrium="improved", collision="srt", tau=0.7)
+    rho, u0 = inputs.random_solenoidal(n, n, n, kmax=8, u_rms=0.02, seed=1, device="cuda")
+    _, tgt = inputs.random_solenoidal(n, n, n, kmax=8, u_rms=0.02, seed=2, device="cuda")
+    u = u0.float().clone().requires_grad_(True)
+    tau = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
+    _, uT = adjoint.simulate(u, tau, steps, n, n, n, precision="f32", equilibrium="improved", collision="srt")
+    L = 0.5 * ((uT.double() - tgt) ** 2).sum()
+    L.backward()
+    g = u.grad.double()
+
+    def loss(uu, t):
+        _, ue = adjoint.forward_only(uu, t, steps, n, n, n, precision="f64", equilibrium="improved",
+                                     collision="srt")
+        return float(0.5 * ((ue - tgt) ** 2).sum())
+
+    rng = np.random.default_rng(3)
+    idx = [tuple(int(rng.integers(0, s)) for s in (3, n, n, n)) for _ in range(64)]
+    h = 1e-5
+    fd, ad = [], []
+    for i in idx:
+        up = u0.clone()
+        um = u0.clone()
+        up[i] += h
+        um[i] -= h
+        fd.append((loss(up, 0.7) - loss(um, 0.7)) / (2 * h))
+        ad.append(float(g[i]))
+    fd, ad = np.array(fd), np.array(ad)
+    err = np.abs(fd - ad).max() / np.abs(fd).max()
+    print("dL/du0: 64-component max-norm relative error vs FD = %.3e" % err)
+    assert err < 1e-3
+    ht = 1e-6
+    fdt = (loss(u0, 0.7 + ht) - loss(u0, 0.7 - ht)) / (2 * ht)
+    print("dL/dtau: adjoint %.9e, FD %.9e" % (float(tau.grad), fdt))
+    assert float(tau.grad) == pytest.approx(fdt, rel=1e-3)
