@@ -215,45 +215,60 @@ def variant_mlups(args, n, **kw):
     return out
 
 
-def adjoint_ratio(args, n=128):
-    """(recomputed forward step + adjoint step) time / forward step time at n^3,
-    FP32, SRT, D3Q19-I, tau = 0.7 (the adjoint workload's lattice)."""
+def adjoint_ratio(args, n=128, horizon=400):
+    """Adjoint cost on the adjoint workload's lattice (periodic n^3, FP32, SRT,
+    D3Q19-I, tau = 0.7): per-step kernel times, and the whole differentiable
+    run (forward with sqrt(T) checkpoints, then backward = recompute + adjoint)
+    through the autograd.Function."""
     import ctypes
 
     import torch
 
-    from paper_1803_04937_gb300 import _lib, inputs
+    from paper_1803_04937_gb300 import _lib, adjoint, inputs
     from paper_1803_04937_gb300.lbm import Simulation
     sim = Simulation(n, n, n, equilibrium="improved", collision="srt", tau=0.7, precision="f32")
     rho, u = inputs.random_solenoidal(n, n, n, kmax=8, u_rms=0.02, seed=1, device="cuda")
+    _, tgt = inputs.random_solenoidal(n, n, n, kmax=8, u_rms=0.02, seed=2, device="cuda")
     sim.init(None, u.float())
     t_fwd = time_steps(sim, 200, 10)
     lib = _lib.load()
     lam = [torch.zeros((19, n, n, n), dtype=torch.float32, device="cuda") for _ in range(2)]
     gw = torch.zeros(2, dtype=torch.float64, device="cuda")
-    state = sim.grids[0]  # any A/B grid is a valid state for timing
+    gwp = ctypes.cast(ctypes.c_void_p(gw.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    state = ctypes.c_void_p(sim.grids[0].data_ptr())  # any A/B grid is a valid state for timing
+    lp = [ctypes.c_void_p(t.data_ptr()) for t in lam]
     s = sim.stream
+    for i in range(10):
+        _lib.check(lib.lbm_adjoint_step(sim.handle, state, lp[i % 2], lp[1 - i % 2], gwp), sim.handle)
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     reps = 200
-    for i in range(10):
-        _lib.check(lib.lbm_adjoint_step(sim.handle, ctypes.c_void_p(state.data_ptr()),
-                                        ctypes.c_void_p(lam[i % 2].data_ptr()),
-                                        ctypes.c_void_p(lam[1 - i % 2].data_ptr()),
-                                        ctypes.cast(ctypes.c_void_p(gw.data_ptr()), ctypes.POINTER(ctypes.c_double))),
-                   sim.handle)
-    torch.cuda.synchronize()
     e0.record(s)
     for i in range(reps):
-        lib.lbm_adjoint_step(sim.handle, ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(lam[i % 2].data_ptr()),
-                             ctypes.c_void_p(lam[1 - i % 2].data_ptr()),
-                             ctypes.cast(ctypes.c_void_p(gw.data_ptr()), ctypes.POINTER(ctypes.c_double)))
+        lib.lbm_adjoint_step(sim.handle, state, lp[i % 2], lp[1 - i % 2], gwp)
     e1.record(s)
     torch.cuda.synchronize()
     t_adj = e0.elapsed_time(e1) * 1e-3 / reps
     sim.close()
-    return {"grid": "%d^3" % n, "forward_ms": t_fwd * 1e3, "adjoint_ms": t_adj * 1e3,
-            "ratio_recompute_plus_adjoint_over_forward": (t_fwd + t_adj) / t_fwd}
+    del lam, sim
+    # whole differentiable run
+    u0 = u.float().clone().requires_grad_(True)
+    tau = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, uT = adjoint.simulate(u0, tau, horizon, n, n, n, precision="f32")
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L = 0.5 * ((uT.double() - tgt) ** 2).sum()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"grid": "%d^3" % n, "horizon": horizon, "forward_step_ms": t_fwd * 1e3, "adjoint_step_ms": t_adj * 1e3,
+            "adjoint_kernel_gbs": 228 * n ** 3 / t_adj / 1e9,
+            "ratio_recompute_plus_adjoint_over_forward": (t_fwd + t_adj) / t_fwd,
+            "forward_pass_s": t1 - t0, "backward_pass_s": t2 - t1,
+            "ratio_backward_over_forward_pass": (t2 - t1) / (t1 - t0)}
 
 
 def e2e(args, n, calls=3, steps_per_call=100):
@@ -411,6 +426,7 @@ def run_native(args):
         for prec in ("f16s", "bf16s"):
             variants[prec] = variant_mlups(args, n, precision=prec)
         variants["aa_" + args.precision] = variant_mlups(args, n, pattern="aa")
+        variants["aa_f16s"] = variant_mlups(args, n, pattern="aa", precision="f16s")
         variants["trt_" + args.precision] = variant_mlups(args, n, collision="trt")
         variants["standard_" + args.precision] = variant_mlups(args, n, equilibrium="standard")
         for k, v in variants.items():

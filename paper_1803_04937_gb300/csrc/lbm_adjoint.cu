@@ -90,10 +90,38 @@ __global__ void k_adjoint_seed(const void *grad_rho, const void *grad_u, int dty
         lam[(long long)q * g.ncell + cell] = L(CX(q) * gu[0] + CY(q) * gu[1] + CZ(q) * gu[2] + gr);
 }
 
+// Collision constants of the adjoint step: the forward step's folded
+// constants (to recompute the collision) plus omega+-, their inverses, kappa
+// and the raw force terms F_q = 3 w_q c_q . a of the pairs.
+template <typename R>
+struct AdjConst {
+    Relax<R> r;
+    R wp, wm, inv_wp, inv_wm, kappa;
+    R fraw[9];
+};
+
+template <typename R>
+static inline AdjConst<R> to_adj(const CollBoth &c)
+{
+    AdjConst<R> a;
+    a.r = to_relax<R>(c);
+    a.wp = R(c.omega_p);
+    a.wm = R(c.omega_m);
+    a.inv_wp = R(1.0 / c.omega_p);
+    a.inv_wm = R(1.0 / c.omega_m);
+    a.kappa = R(c.kappa);
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        a.fraw[k] = R(3.0 * WQ<double>(q) * 2.0 *
+                      (CX(q) * c.half_a[0] + CY(q) * c.half_a[1] + CZ(q) * c.half_a[2]));
+    }
+    return a;
+}
+
 template <typename T, typename L>
 __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ state, const L *__restrict__ lam_next,
                                                       L *__restrict__ lam, double *partial, Geo g,
-                                                      Coll<typename Storage<T>::R> p)
+                                                      AdjConst<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     __shared__ double sh[32];
@@ -104,11 +132,30 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
     if (x < g.nx && y < g.ny) {
         Cell c(x, y, z, g);
         const int self = c.self();
+        // forward quantities of the cell at time t (rho0 = 1)
         R f[Q];
         gather<AB>(state, c, g.ncell, f);
-        R drho, rho0, u[3];
-        macro(f, p, drho, rho0, u);
-        const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        R sf[9], df[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            sf[k] = f[2 * k + 1] + f[2 * k + 2];
+            df[k] = f[2 * k + 1] - f[2 * k + 2];
+        }
+        const R drho = f[0] + (((sf[0] + sf[1]) + (sf[2] + sf[3])) + ((sf[4] + sf[5]) + (sf[6] + sf[7])) + sf[8]);
+        R u[3] = {p.r.half_a[0], p.r.half_a[1], p.r.half_a[2]};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            if (CX(q)) u[0] += R(CX(q)) * df[k];
+            if (CY(q)) u[1] += R(CY(q)) * df[k];
+            if (CZ(q)) u[2] += R(CZ(q)) * df[k];
+        }
+        const R u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
+        const R uu = u2[0] + u2[1] + u2[2];
+        const R base = drho - R(1.5) * uu;
+        const R Bf = p.r.cf * base - p.r.kf * uu;
+        const R Be[3] = {p.r.ce * base + p.r.ke * u2[0], p.r.ce * base + p.r.ke * u2[1],
+                         p.r.ce * base + p.r.ke * u2[2]};
         // S^T: the value that left x along c_q arrived at x + c_q (or, through
         // a wall, at the opposite slot of x).
         R mu[Q];
@@ -119,47 +166,76 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
             long long off = wall ? (long long)OPP(q) * g.ncell + self : (long long)q * g.ncell + dst;
             mu[q] = R(lam_next[off]);
         }
-        // omega gradients (per cell), and nu
-        R nu[Q];
-        R eq0 = rest_equilibrium(uu, drho, rho0, p.kappa);
-        R cgp = mu[0] * (f[0] - eq0);
-        R cgm = R(0);
-        nu[0] = p.omega_p * mu[0];
-        R fa = R(0);  // sum_q mu_q F_q / 3, F_q = 3 w_q c_q . a
-#define LBM_ADJ_PAIR(k)                                                                    \
-    {                                                                                      \
-        constexpr int q = 2 * k + 1;                                                       \
-        R sym, asym;                                                                       \
-        pair_equilibrium<R, q>(u, uu, drho, rho0, p.kappa, sym, asym);                     \
-        R mp = R(0.5) * (mu[q] + mu[q + 1]);                                               \
-        R mm = R(0.5) * (mu[q] - mu[q + 1]);                                               \
-        cgp += mp * (f[q] + f[q + 1] - R(2) * sym);                                         \
-        cgm += mm * (f[q] - f[q + 1] - R(2) * asym);                                        \
-        fa += (mu[q] - mu[q + 1]) * WQ<R>(q) *                                             \
-              R(2) * (R(CX(q)) * p.half_a[0] + R(CY(q)) * p.half_a[1] + R(CZ(q)) * p.half_a[2]); \
-        nu[q] = p.omega_p * mp + p.omega_m * mm;                                           \
-        nu[q + 1] = p.omega_p * mp - p.omega_m * mm;                                       \
-    }
-        LBM_ADJ_PAIR(0) LBM_ADJ_PAIR(1) LBM_ADJ_PAIR(2) LBM_ADJ_PAIR(3) LBM_ADJ_PAIR(4)
-        LBM_ADJ_PAIR(5) LBM_ADJ_PAIR(6) LBM_ADJ_PAIR(7) LBM_ADJ_PAIR(8)
-#undef LBM_ADJ_PAIR
-        gp_acc = -(double)cgp;
-        gm_acc = -(double)cgm - 0.5 * 3.0 * (double)fa;
-        R G[3], A;
-        contract_dfeq_du(nu, u, p.kappa, G, A);
-        lam[self] = L(mu[0] - p.omega_p * mu[0] + A);
+        // omega gradients: sum_q mu+_q (f - feq)_q = [mu0 (omega+ f0 - omega+ feq0) + sum_k S_k a1_k] / omega+,
+        // sum_q mu-_q (f - feq)_q = sum_k D_k a2_k / omega-, a1/a2 the forward step's relaxation terms.
+        R cgp = mu[0] * (p.wp * f[0] - (p.r.c0 * base + p.r.k0 * uu));
+        R cgm = R(0), cf_ = R(0);
+        R Ssum_f = R(0), Ssum_e = R(0);
+        R face[3] = {R(0), R(0), R(0)}, edge[3] = {R(0), R(0), R(0)};
+        R Bd[3] = {R(0), R(0), R(0)};
+        R cxx = R(0), cyy = R(0), czz = R(0), cxy = R(0), cxz = R(0), cyz = R(0);
+        R S[9], D[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int q = 2 * k + 1;
-            R mp = R(0.5) * (mu[q] + mu[q + 1]);
-            R mm = R(0.5) * (mu[q] - mu[q + 1]);
-            R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
-            lam[(long long)q * g.ncell + self] = L(mu[q] - p.omega_p * mp - p.omega_m * mm + A + cg);
-            lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] - p.omega_p * mp + p.omega_m * mm + A - cg);
+            S[k] = mu[q] + mu[q + 1];
+            D[k] = mu[q] - mu[q + 1];
+            const R cu = R(CX(q)) * u[0] + R(CY(q)) * u[1] + R(CZ(q)) * u[2];
+            R tsym, tasym;
+            const R w = WQ<R>(q);
+            if (NORM2(q) == 1) {
+                const int a = CX(q) ? 0 : (CY(q) ? 1 : 2);
+                tsym = Bf + p.r.Kf * u2[a];
+                tasym = p.r.Af * cu;
+                Ssum_f += S[k];
+                face[a] += S[k];
+            } else {
+                const int e = CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2);
+                tsym = Be[e] + p.r.Ke * (cu * cu);
+                tasym = p.r.Ae * cu;
+                Ssum_e += S[k];
+                edge[e] += S[k];
+            }
+            cgp += S[k] * (p.r.hp * sf[k] - tsym);
+            cgm += D[k] * (p.r.hm * df[k] - tasym);
+            cf_ += D[k] * p.fraw[k];
+            const R wD = w * D[k], wS = w * S[k];
+            if (CX(q)) Bd[0] += R(CX(q)) * wD;
+            if (CY(q)) Bd[1] += R(CY(q)) * wD;
+            if (CZ(q)) Bd[2] += R(CZ(q)) * wD;
+            if (CX(q)) cxx += wS;
+            if (CY(q)) cyy += wS;
+            if (CZ(q)) czz += wS;
+            if (CX(q) * CY(q)) cxy += R(CX(q) * CY(q)) * wS;
+            if (CX(q) * CZ(q)) cxz += R(CX(q) * CZ(q)) * wS;
+            if (CY(q) * CZ(q)) cyz += R(CY(q) * CZ(q)) * wS;
+        }
+        gp_acc = -(double)(cgp * p.inv_wp);
+        gm_acc = -(double)(cgm * p.inv_wm) - 0.5 * (double)cf_;
+        // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
+        const R A = p.wp * (WQ<R>(0) * mu[0] + WQ<R>(1) * Ssum_f + WQ<R>(7) * Ssum_e);
+        const R cu3[3] = {cxx * u[0] + cxy * u[1] + cxz * u[2], cxy * u[0] + cyy * u[1] + cyz * u[2],
+                          cxz * u[0] + cyz * u[1] + czz * u[2]};
+        const R fs = face[0] + face[1] + face[2];
+        R G[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const R gs = R(3) * p.wm * Bd[i] + R(9) * p.wp * cu3[i] - R(3) * A * u[i];
+            const R gd = p.wp * (mu[0] * (R(1) / R(3)) - (fs - face[i]) * (R(1) / R(6)) + edge[i] * (R(1) / R(12)));
+            G[i] = gs + p.kappa * gd * u[i];
+        }
+        lam[self] = L(p.r.one_m_wp * mu[0] + A);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            const R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
+            const R t = A - p.r.hp * S[k];
+            const R hd = p.r.hm * D[k];
+            lam[(long long)q * g.ncell + self] = L(mu[q] + t - hd + cg);
+            lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] + t + hd - cg);
         }
     }
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    // block_sum expects a 1D thread index; fold the 2D block into it.
     double s0 = gp_acc, s1 = gm_acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -234,7 +310,7 @@ static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam
                               const Geo &g, const CollBoth &cb, cudaStream_t s)
 {
     using R = typename Storage<T>::R;
-    Coll<R> p = to_coll<R>(cb);
+    AdjConst<R> p = to_adj<R>(cb);
     k_adjoint_step<T, L><<<adj_grid(g), adj_block(), 0, s>>>((const T *)state, (const L *)lam_next, (L *)lam,
                                                               scratch, g, p);
     cudaError_t e = cudaGetLastError();

@@ -22,6 +22,7 @@ struct lbm_ctx {
     int rho0_mode = 0;
     int pattern = LBM_PATTERN_AB;
     int bx = 128, by = 2;
+    int cells_x = 1;
     void *a = nullptr, *b = nullptr;
     double *scratch = nullptr;
     cudaStream_t stream = nullptr;
@@ -186,6 +187,8 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
         h->bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
         h->by = 256 / h->bx;
     }
+    // 16-bit storage needs paired accesses to reach the bandwidth roofline
+    h->cells_x = (precision == LBM_F16S || precision == LBM_BF16S) ? 2 : 1;
     *out = h;
     return LBM_OK;
 }
@@ -240,6 +243,10 @@ int lbm_set_option(lbm_handle h, int key, double v)
         if (v != LBM_SRT && v != LBM_TRT) return fail(h, LBM_EINVAL, "bad collision");
         h->collision = (int)v;
         return LBM_OK;
+    case LBM_OPT_CELLS_X:
+        if (v != 1.0 && v != 2.0) return fail(h, LBM_EINVAL, "cells per thread must be 1 or 2");
+        h->cells_x = (int)v;
+        return LBM_OK;
     case LBM_OPT_BLOCK_X:
     case LBM_OPT_BLOCK_Y: {
         int bx = key == LBM_OPT_BLOCK_X ? (int)v : h->bx;
@@ -270,6 +277,7 @@ int lbm_get_option(lbm_handle h, int key, double *v)
     case LBM_OPT_TAU: *v = h->tau; return LBM_OK;
     case LBM_OPT_EQUILIBRIUM: *v = h->equilibrium; return LBM_OK;
     case LBM_OPT_COLLISION: *v = h->collision; return LBM_OK;
+    case LBM_OPT_CELLS_X: *v = h->cells_x; return LBM_OK;
     case LBM_OPT_BLOCK_X: *v = h->bx; return LBM_OK;
     case LBM_OPT_BLOCK_Y: *v = h->by; return LBM_OK;
     }
@@ -324,7 +332,7 @@ int lbm_step(lbm_handle h, int n)
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised (lbm_init or lbm_set_pdfs)");
     const lbm::Geo g = geo(h);
     const lbm::CollBoth c = coll(h);
-    const lbm::LaunchShape shape{h->bx, h->by};
+    const lbm::LaunchShape shape{h->bx, h->by, h->cells_x};
     for (int i = 0; i < n; ++i) {
         cudaError_t e;
         if (h->pattern == LBM_PATTERN_AB) {

@@ -13,7 +13,8 @@ enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
 
 // Layout of the current state (see lbm_device.cuh): 0 AB, 1 AA even, 2 AA odd.
 struct LaunchShape {
-    int bx, by;  // thread block (bx * by threads, bx along x)
+    int bx, by;   // thread block (bx * by threads, bx along x)
+    int cells_x;  // cells per thread along x: 1, or 2 (used when nx is even)
 };
 
 // Collision constants for both arithmetic types; the launcher picks one.

@@ -1,21 +1,30 @@
 // Fused stream + collide time step (Eq. 15; D3Q19-S / D3Q19-I equilibria;
 // SRT / TRT; periodic or half-way bounce-back; Buick-Greated force).
 //
-// One thread updates one cell: it gathers the 19 populations that stream into
-// the cell, collides them in registers (FP32, or FP64 for FP64 storage), and
-// stores the 19 post-collision values.  Structure-of-arrays storage gives
-// coalesced accesses along x for every population; the +-x populations are
-// read one element off alignment, which L1/L2 absorb without extra DRAM
-// traffic.  The algorithmic traffic is 19 loads + 19 stores per cell.
+// Each thread gathers the populations that stream into its cell(s), collides
+// them in registers (FP32, or FP64 for FP64 storage) and stores the
+// post-collision values.  Structure-of-arrays storage gives coalesced accesses
+// along x for every population.  Algorithmic traffic: 19 loads + 19 stores
+// per cell.
+//
+// Two thread mappings:
+//  - one cell per thread (any nx): scalar loads; the +-x populations are read
+//    one element off alignment, which L1/L2 absorb without extra DRAM traffic.
+//  - two neighbouring cells per thread (nx even): every population is read
+//    and written as an aligned pair (half2 / bfloat162 / float2 / double2);
+//    a +-x shifted pair is assembled from the own pair and one element of the
+//    neighbouring lane's pair (warp shuffle), with one scalar load at the
+//    warp's edge.  Halves the load/store instructions and the per-cell index
+//    arithmetic, which the 16-bit formats need to reach the HBM roofline.
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
 namespace lbm {
 
-// A/B pull step: gather from src (layout AB), write dst in layout AB.
-template <typename T>
+// A/B pull step, one cell per thread: gather from src (layout AB), write dst.
+template <typename T, bool RHO0>
 __global__ void __launch_bounds__(256) k_step_ab(const T *__restrict__ src, T *__restrict__ dst, Geo g,
-                                                 Coll<typename Storage<T>::R> p)
+                                                 Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -25,15 +34,134 @@ __global__ void __launch_bounds__(256) k_step_ab(const T *__restrict__ src, T *_
     Cell c(x, y, z, g);
     R f[Q];
     gather<AB>(src, c, g.ncell, f);
-    collide(f, p);
+    collide_lean<R, RHO0>(f, p);
     scatter<D_AB_NEXT>(dst, c, g.ncell, f);
+}
+
+// ---------------------------------------------------------------- pairs
+
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    static __device__ __forceinline__ void load(const float *p, float &a, float &b)
+    {
+        float2 v = *reinterpret_cast<const float2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void store(float *p, float a, float b)
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+};
+template <> struct Pair<double> {
+    static __device__ __forceinline__ void load(const double *p, double &a, double &b)
+    {
+        double2 v = *reinterpret_cast<const double2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void store(double *p, double a, double b)
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+    }
+};
+template <> struct Pair<__half> {
+    static __device__ __forceinline__ void load(const __half *p, float &a, float &b)
+    {
+        __half2 v = *reinterpret_cast<const __half2 *>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    static __device__ __forceinline__ void store(__half *p, float a, float b)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float &a, float &b)
+    {
+        __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float a, float b)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// A/B pull step, two cells (x0, x0 + 1) per thread, x0 even, nx even.
+// blockDim.x is a multiple of 32, so a warp never spans two lattice rows and
+// lane 0 of a warp starts a 64-cell segment of its row.
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(256) k_step_ab2(const T *__restrict__ src, T *__restrict__ dst, Geo g,
+                                                  Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    const int xs = active ? x0 : 0;  // inactive lanes read a valid pair and take part in the shuffles
+    Cell c(xs, y, z, g);
+    const int own = z * c.nxy + y * c.nx;
+    R f0[Q], f1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q), cy = CY(q), cz = CZ(q);
+        const int ys = cy == 0 ? y : (cy > 0 ? c.ym : c.yp);
+        const int zs = cz == 0 ? z : (cz > 0 ? c.zm : c.zp);
+        bool wyz = false;
+        if (cy > 0) wyz |= c.bym;
+        if (cy < 0) wyz |= c.byp;
+        if (cz > 0) wyz |= c.bzm;
+        if (cz < 0) wyz |= c.bzp;
+        const T *plane = src + (long long)q * g.ncell;
+        const T *oplane = src + (long long)OPP(q) * g.ncell;
+        const int srow = zs * c.nxy + ys * c.nx;
+        // through a y/z wall both cells bounce back: their own opposite pair
+        const T *pp = wyz ? oplane + own + xs : plane + srow + xs;
+        R lo, hi;
+        Pair<T>::load(pp, lo, hi);
+        if (cx == 0) {
+            f0[q] = lo;
+            f1[q] = hi;
+        } else if (cx > 0) {  // pull from x - 1
+            R left = __shfl_up_sync(0xffffffffu, hi, 1);
+            if (lane == 0 && active && !wyz) {
+                if (x0 == 0 && g.wall_x)
+                    left = Storage<T>::load(oplane + own + x0);
+                else
+                    left = Storage<T>::load(plane + srow + (x0 == 0 ? g.nx - 1 : x0 - 1));
+            }
+            f0[q] = wyz ? lo : left;
+            f1[q] = wyz ? hi : lo;
+        } else {  // pull from x + 1
+            R right = __shfl_down_sync(0xffffffffu, lo, 1);
+            if ((lane == 31 || x0 + 2 >= g.nx) && active && !wyz) {
+                if (x0 + 2 >= g.nx && g.wall_x)
+                    right = Storage<T>::load(oplane + own + x0 + 1);
+                else
+                    right = Storage<T>::load(plane + srow + (x0 + 2 >= g.nx ? 0 : x0 + 2));
+            }
+            f0[q] = wyz ? lo : hi;
+            f1[q] = wyz ? hi : right;
+        }
+    }
+    if (!active) return;
+    collide_lean<R, RHO0>(f0, p);
+    collide_lean<R, RHO0>(f1, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Pair<T>::store(dst + (long long)q * g.ncell + own + x0, f0[q], f1[q]);
 }
 
 // AA in-place steps.  Even: own cell only (read q, write qbar).  Odd: read
 // qbar at x - c_q, write q at x + c_q (bounce-back through walls stays in the
 // own cell).  Every location is read and written by exactly one thread.
-template <typename T, int ODD>
-__global__ void __launch_bounds__(256) k_step_aa(T *grid, Geo g, Coll<typename Storage<T>::R> p)
+template <typename T, int ODD, bool RHO0>
+__global__ void __launch_bounds__(256) k_step_aa(T *grid, Geo g, Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -44,40 +172,79 @@ __global__ void __launch_bounds__(256) k_step_aa(T *grid, Geo g, Coll<typename S
     R f[Q];
     if (ODD) {
         gather<AA_ODD>(grid, c, g.ncell, f);
-        collide(f, p);
+        collide_lean<R, RHO0>(f, p);
         scatter<D_AA_ODD>(grid, c, g.ncell, f);
     } else {
         gather<AA_EVEN>(grid, c, g.ncell, f);
-        collide(f, p);
+        collide_lean<R, RHO0>(f, p);
         scatter<D_AA_EVEN>(grid, c, g.ncell, f);
     }
 }
 
-template <typename T>
+// AA even step, two cells per thread: purely local, so every access is an
+// aligned pair.
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(256) k_step_aa_even2(T *grid, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= g.nx || y >= g.ny) return;
+    const long long own = ((long long)z * g.ny + y) * g.nx + x0;
+    R f0[Q], f1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Pair<T>::load(grid + (long long)q * g.ncell + own, f0[q], f1[q]);
+    collide_lean<R, RHO0>(f0, p);
+    collide_lean<R, RHO0>(f1, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Pair<T>::store(grid + (long long)OPP(q) * g.ncell + own, f0[q], f1[q]);
+}
+
+template <typename T, bool RHO0>
 static cudaError_t step_t(int kind, const void *src, void *dst, const Geo &g, const CollBoth &cb, LaunchShape s,
                           cudaStream_t stream)
 {
     using R = typename Storage<T>::R;
-    Coll<R> p = to_coll<R>(cb);
+    Relax<R> p = to_relax<R>(cb);
     dim3 block(s.bx, s.by, 1);
-    dim3 grid((g.nx + s.bx - 1) / s.bx, (g.ny + s.by - 1) / s.by, g.nz);
-    if (kind == 0)
-        k_step_ab<T><<<grid, block, 0, stream>>>((const T *)src, (T *)dst, g, p);
-    else if (kind == 1)
-        k_step_aa<T, 0><<<grid, block, 0, stream>>>((T *)dst, g, p);
-    else
-        k_step_aa<T, 1><<<grid, block, 0, stream>>>((T *)dst, g, p);
+    const bool pairs = s.cells_x == 2 && (g.nx % 2) == 0 && (s.bx % 32) == 0;
+    const int span = pairs ? 2 * s.bx : s.bx;
+    dim3 grid((g.nx + span - 1) / span, (g.ny + s.by - 1) / s.by, g.nz);
+    if (kind == 0) {
+        if (pairs)
+            k_step_ab2<T, RHO0><<<grid, block, 0, stream>>>((const T *)src, (T *)dst, g, p);
+        else
+            k_step_ab<T, RHO0><<<grid, block, 0, stream>>>((const T *)src, (T *)dst, g, p);
+    } else if (kind == 1) {
+        if (pairs)
+            k_step_aa_even2<T, RHO0><<<grid, block, 0, stream>>>((T *)dst, g, p);
+        else
+            k_step_aa<T, 0, RHO0><<<grid, block, 0, stream>>>((T *)dst, g, p);
+    } else {
+        // the odd AA step writes to x + c_q: one cell per thread
+        dim3 grid1((g.nx + s.bx - 1) / s.bx, (g.ny + s.by - 1) / s.by, g.nz);
+        k_step_aa<T, 1, RHO0><<<grid1, block, 0, stream>>>((T *)dst, g, p);
+    }
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t step_rho0(int kind, const void *src, void *dst, const Geo &g, const CollBoth &cb, LaunchShape s,
+                            cudaStream_t stream)
+{
+    return cb.rho0_is_rho ? step_t<T, true>(kind, src, dst, g, cb, s, stream)
+                          : step_t<T, false>(kind, src, dst, g, cb, s, stream);
 }
 
 cudaError_t launch_step(int prec, int kind, const void *src, void *dst, const Geo &g, const CollBoth &c,
                         LaunchShape s, cudaStream_t stream)
 {
     switch (prec) {
-    case P_F64: return step_t<double>(kind, src, dst, g, c, s, stream);
-    case P_F32: return step_t<float>(kind, src, dst, g, c, s, stream);
-    case P_F16: return step_t<__half>(kind, src, dst, g, c, s, stream);
-    case P_BF16: return step_t<__nv_bfloat16>(kind, src, dst, g, c, s, stream);
+    case P_F64: return step_rho0<double>(kind, src, dst, g, c, s, stream);
+    case P_F32: return step_rho0<float>(kind, src, dst, g, c, s, stream);
+    case P_F16: return step_rho0<__half>(kind, src, dst, g, c, s, stream);
+    case P_BF16: return step_rho0<__nv_bfloat16>(kind, src, dst, g, c, s, stream);
     }
     return cudaErrorInvalidValue;
 }

@@ -27,25 +27,33 @@ CASES = [
 ]
 
 
-def _run_gpu(shape, rho, u, steps, precision, pattern, case):
+def _run_gpu(shape, rho, u, steps, precision, pattern, case, cells_x=None):
     from paper_1803_04937_gb300.lbm import Simulation
     nz, ny, nx = shape
-    sim = Simulation(nx, ny, nz, precision=precision, pattern=pattern, **case)
+    sim = Simulation(nx, ny, nz, precision=precision, pattern=pattern, cells_x=cells_x, **case)
     sim.init(rho.cuda(), u.cuda())
     sim.step(steps)
     r, uu = sim.moments(torch.float64)
     return sim, r.cpu().numpy(), uu.cpu().numpy()
 
 
+# (nx, cells per thread): odd nx with one cell per thread; even nx = 130 with two
+# cells per thread spans three warps of a row, a ragged last warp and the
+# cross-warp / wrap-around edge loads of the paired kernel.
+MAPPINGS = [(37, 1), (130, 2)]
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
+@pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_step_matches_oracle(case, pattern, precision):
+def test_step_matches_oracle(case, mapping, pattern, precision):
     kw = CASES[case]
-    shape = (5, 9, 37)  # nz, ny, nx: odd sizes, ragged x blocks
+    nx, cells_x = mapping
+    shape = (5, 9, nx)  # nz, ny, nx
     rho, u = random_fields(shape, seed=100 + case)
     steps = 7 if pattern == "aa" else 6  # odd count leaves AA in its odd layout
-    sim, r_g, u_g = _run_gpu(shape, rho, u, steps, precision, pattern, kw)
+    sim, r_g, u_g = _run_gpu(shape, rho, u, steps, precision, pattern, kw, cells_x=cells_x)
     cfg = oracle_config(shape[2], shape[1], shape[0], **kw)
     f_o = oracle.step(cfg, oracle.init(cfg, rho.numpy(), u.numpy()), steps)
     r_o, u_o = oracle.moments(cfg, f_o)
@@ -57,15 +65,19 @@ def test_step_matches_oracle(case, pattern, precision):
 
 @pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s", "f64"])
 @pytest.mark.parametrize("case", [0, 3, 5])
-def test_aa_equals_ab_bitwise(case, precision):
-    """AA and A/B run the same arithmetic per cell: identical bits after any
-    number of steps (also a race check of the in-place pattern)."""
+@pytest.mark.parametrize("nx", [45, 130])
+def test_aa_equals_ab_bitwise(nx, case, precision):
+    """AA and A/B, with one or two cells per thread, run the same arithmetic per
+    cell: identical bits after any number of steps (also a race check of the
+    in-place pattern)."""
     kw = CASES[case]
-    shape = (6, 11, 45)
+    shape = (6, 11, nx)
     rho, u = random_fields(shape, seed=7)
     for steps in (1, 4, 9):
-        sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw)
-        sb, _, _ = _run_gpu(shape, rho, u, steps, precision, "aa", kw)
+        sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=1)
+        sb, _, _ = _run_gpu(shape, rho, u, steps, precision, "aa", kw, cells_x=2)
+        sc, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=2)
+        assert torch.equal(sa.get_pdfs(), sc.get_pdfs())
         assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
         ra, ua = sa.moments(torch.float32)
         rb, ub = sb.moments(torch.float32)
@@ -120,12 +132,13 @@ def test_reductions_match_oracle_and_flag_nonfinite():
 
 
 @pytest.mark.parametrize("precision,bound", [("f16s", 2e-3), ("bf16s", 2e-2)])
-def test_16bit_storage_error_is_bounded(precision, bound):
+@pytest.mark.parametrize("cells_x", [1, 2])
+def test_16bit_storage_error_is_bounded(cells_x, precision, bound):
     """16-bit shifted storage: velocity error against the FP64 oracle, stated."""
     shape = (8, 16, 64)
     rho, u = random_fields(shape, seed=21, amp=0.05, drho=0.0)
     kw = dict(equilibrium="improved", collision="srt", tau=0.8)
-    _, _, u_g = _run_gpu(shape, rho, u, 20, precision, "ab", kw)
+    _, _, u_g = _run_gpu(shape, rho, u, 20, precision, "ab", kw, cells_x=cells_x)
     cfg = oracle_config(64, 16, 8, **kw)
     _, u_o = oracle.run(cfg, rho.numpy(), u.numpy(), 20)
     err = rel_maxnorm(u_g, u_o)
@@ -138,15 +151,17 @@ def test_tiny_and_degenerate_lattices():
     walls on a 1-cell axis all agree with the oracle."""
     for shape, walls in [((1, 1, 1), (False, False, False)), ((1, 1, 7), (False, False, False)),
                          ((3, 1, 1), (False, False, True)), ((1, 5, 1), (False, True, False)),
-                         ((2, 1, 3), (True, True, False))]:
+                         ((2, 1, 3), (True, True, False)), ((2, 3, 2), (True, False, False)),
+                         ((1, 1, 2), (False, False, False)), ((3, 2, 4), (True, True, True))]:
         kw = dict(collision="trt", tau=0.7, force=(1e-4, 2e-4, -1e-4), walls=walls)
         rho, u = random_fields(shape, seed=5)
-        _, _, u_g = _run_gpu(shape, rho, u, 5, "f64", "ab", kw)
-        _, _, u_a = _run_gpu(shape, rho, u, 5, "f64", "aa", kw)
         cfg = oracle_config(shape[2], shape[1], shape[0], **kw)
         _, u_o = oracle.run(cfg, rho.numpy(), u.numpy(), 5)
-        assert rel_maxnorm(u_g, u_o) < 1e-12, shape
-        assert rel_maxnorm(u_a, u_o) < 1e-12, shape
+        for cells_x in (1, 2):
+            _, _, u_g = _run_gpu(shape, rho, u, 5, "f64", "ab", kw, cells_x=cells_x)
+            _, _, u_a = _run_gpu(shape, rho, u, 5, "f64", "aa", kw, cells_x=cells_x)
+            assert rel_maxnorm(u_g, u_o) < 1e-12, (shape, cells_x)
+            assert rel_maxnorm(u_a, u_o) < 1e-12, (shape, cells_x)
 
 
 def test_zero_steps_returns_initial_fields():
