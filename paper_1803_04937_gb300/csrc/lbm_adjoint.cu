@@ -132,9 +132,18 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
     if (x < g.nx && y < g.ny) {
         Cell c(x, y, z, g);
         const int self = c.self();
-        // forward quantities of the cell at time t (rho0 = 1)
-        R f[Q];
+        // forward quantities of the cell at time t (rho0 = 1), and S^T: the
+        // value that left x along c_q arrived at x + c_q (or, through a wall,
+        // at the opposite slot of x).  All 38 loads are issued first.
+        R f[Q], mu[Q];
         gather<AB>(state, c, g.ncell, f);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            bool wall;
+            int dst = c.template along<1>(q, wall);
+            long long off = wall ? (long long)OPP(q) * g.ncell + self : (long long)q * g.ncell + dst;
+            mu[q] = R(lam_next[off]);
+        }
         R sf[9], df[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -156,16 +165,6 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
         const R Bf = p.r.cf * base - p.r.kf * uu;
         const R Be[3] = {p.r.ce * base + p.r.ke * u2[0], p.r.ce * base + p.r.ke * u2[1],
                          p.r.ce * base + p.r.ke * u2[2]};
-        // S^T: the value that left x along c_q arrived at x + c_q (or, through
-        // a wall, at the opposite slot of x).
-        R mu[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            bool wall;
-            int dst = c.template along<1>(q, wall);
-            long long off = wall ? (long long)OPP(q) * g.ncell + self : (long long)q * g.ncell + dst;
-            mu[q] = R(lam_next[off]);
-        }
         // omega gradients: sum_q mu+_q (f - feq)_q = [mu0 (omega+ f0 - omega+ feq0) + sum_k S_k a1_k] / omega+,
         // sum_q mu-_q (f - feq)_q = sum_k D_k a2_k / omega-, a1/a2 the forward step's relaxation terms.
         R cgp = mu[0] * (p.wp * f[0] - (p.r.c0 * base + p.r.k0 * uu));

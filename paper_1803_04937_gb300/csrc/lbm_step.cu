@@ -107,47 +107,59 @@ __global__ void __launch_bounds__(256) k_step_ab2(const T *__restrict__ src, T *
     const int xs = active ? x0 : 0;  // inactive lanes read a valid pair and take part in the shuffles
     Cell c(xs, y, z, g);
     const int own = z * c.nxy + y * c.nx;
-    R f0[Q], f1[Q];
+    // Phase 1: issue every load before any shuffle (shuffles wait for their
+    // operand, and interleaving them with the loads would serialise memory
+    // latencies).  lo/hi: the own pair of the source row (or, through a y/z
+    // wall, the own cell's opposite-slot pair); e: the element beyond the
+    // warp's edge for the +-x populations, loaded only by the edge lane.
+    R lo[Q], hi[Q], e[Q];
+    bool wyz[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q), cy = CY(q), cz = CZ(q);
         const int ys = cy == 0 ? y : (cy > 0 ? c.ym : c.yp);
         const int zs = cz == 0 ? z : (cz > 0 ? c.zm : c.zp);
-        bool wyz = false;
-        if (cy > 0) wyz |= c.bym;
-        if (cy < 0) wyz |= c.byp;
-        if (cz > 0) wyz |= c.bzm;
-        if (cz < 0) wyz |= c.bzp;
+        bool w = false;
+        if (cy > 0) w |= c.bym;
+        if (cy < 0) w |= c.byp;
+        if (cz > 0) w |= c.bzm;
+        if (cz < 0) w |= c.bzp;
+        wyz[q] = w;
         const T *plane = src + (long long)q * g.ncell;
         const T *oplane = src + (long long)OPP(q) * g.ncell;
         const int srow = zs * c.nxy + ys * c.nx;
-        // through a y/z wall both cells bounce back: their own opposite pair
-        const T *pp = wyz ? oplane + own + xs : plane + srow + xs;
-        R lo, hi;
-        Pair<T>::load(pp, lo, hi);
+        Pair<T>::load(w ? oplane + own + xs : plane + srow + xs, lo[q], hi[q]);
+        e[q] = R(0);
+        if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
+            const bool need = lane == 0 && active && !w;
+            const T *a = (x0 == 0 && g.wall_x) ? oplane + own + xs
+                                                : plane + srow + (xs == 0 ? g.nx - 1 : xs - 1);
+            if (need) e[q] = Storage<T>::load(a);
+        } else if (cx < 0) {  // pull from x + 1: the last lane of a segment needs element x0 + 2
+            const bool need = (lane == 31 || xs + 2 >= g.nx) && active && !w;
+            const T *a = (xs + 2 >= g.nx && g.wall_x) ? oplane + own + xs + 1
+                                                       : plane + srow + (xs + 2 >= g.nx ? 0 : xs + 2);
+            if (need) e[q] = Storage<T>::load(a);
+        }
+    }
+    // Phase 2: assemble the shifted pairs.
+    R f0[Q], f1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
         if (cx == 0) {
-            f0[q] = lo;
-            f1[q] = hi;
-        } else if (cx > 0) {  // pull from x - 1
-            R left = __shfl_up_sync(0xffffffffu, hi, 1);
-            if (lane == 0 && active && !wyz) {
-                if (x0 == 0 && g.wall_x)
-                    left = Storage<T>::load(oplane + own + x0);
-                else
-                    left = Storage<T>::load(plane + srow + (x0 == 0 ? g.nx - 1 : x0 - 1));
-            }
-            f0[q] = wyz ? lo : left;
-            f1[q] = wyz ? hi : lo;
-        } else {  // pull from x + 1
-            R right = __shfl_down_sync(0xffffffffu, lo, 1);
-            if ((lane == 31 || x0 + 2 >= g.nx) && active && !wyz) {
-                if (x0 + 2 >= g.nx && g.wall_x)
-                    right = Storage<T>::load(oplane + own + x0 + 1);
-                else
-                    right = Storage<T>::load(plane + srow + (x0 + 2 >= g.nx ? 0 : x0 + 2));
-            }
-            f0[q] = wyz ? lo : hi;
-            f1[q] = wyz ? hi : right;
+            f0[q] = lo[q];
+            f1[q] = hi[q];
+        } else if (cx > 0) {
+            R left = __shfl_up_sync(0xffffffffu, hi[q], 1);
+            if (lane == 0) left = e[q];
+            f0[q] = wyz[q] ? lo[q] : left;
+            f1[q] = wyz[q] ? hi[q] : lo[q];
+        } else {
+            R right = __shfl_down_sync(0xffffffffu, lo[q], 1);
+            if (lane == 31 || xs + 2 >= g.nx) right = e[q];
+            f0[q] = wyz[q] ? lo[q] : hi[q];
+            f1[q] = wyz[q] ? hi[q] : right;
         }
     }
     if (!active) return;

@@ -1,0 +1,199 @@
+"""The D3Q19 workloads at their full sizes, checked against the FP64 oracle on
+sampled outputs it can compute (a y,z- or x,z-invariant flow is one oracle
+column) and against properties that hold at any size.  Each test prints the
+measured errors."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1803_04937_gb300 import inputs
+from tests._helpers import oracle_config, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(nx, ny, nz, **kw):
+    from paper_1803_04937_gb300.lbm import Simulation
+    return Simulation(nx, ny, nz, **kw)
+
+
+# ------------------------------------------------------------------ Taylor-Green 32^3, FP64
+
+@pytest.mark.parametrize("equilibrium", ["standard", "improved"])
+def test_taylor_green_32_fp64(equilibrium):
+    """Periodic 32^3, FP64, TGV u0 = 0.05, tau = 0.8, 100 steps: velocity field
+    and energy series vs the oracle (<= 1e-12), decay rate vs 2 nu |k|^2."""
+    n, steps = 32, 100
+    rho, u = inputs.taylor_green(n, u0=0.05)
+    kw = dict(equilibrium=equilibrium, collision="srt", tau=0.8)
+    sim = _sim(n, n, n, precision="f64", **kw)
+    sim.init(rho.cuda(), u.cuda())
+    cfg = oracle_config(n, n, n, **kw)
+    f = oracle.init(cfg, rho.numpy(), u.numpy())
+    e_gpu, e_or = [sim.reduce()["energy"]], []
+    e_or.append(0.5 * (oracle.moments(cfg, f)[1] ** 2).sum())
+    for _ in range(steps // 10):
+        sim.step(10)
+        f = oracle.step(cfg, f, 10)
+        e_gpu.append(sim.reduce()["energy"])
+        e_or.append(0.5 * (oracle.moments(cfg, f)[1] ** 2).sum())
+    _, ug = sim.moments()
+    _, uo = oracle.moments(cfg, f)
+    err = rel_maxnorm(ug.cpu().numpy(), uo)
+    e_err = max(abs(a - b) / b for a, b in zip(e_gpu, e_or))
+    nu, k2 = (0.8 - 0.5) / 3, 3 * (2 * math.pi / n) ** 2
+    rate = -np.polyfit(np.arange(len(e_gpu)) * 10.0, np.log(e_gpu), 1)[0]
+    print("TGV32 %s: |u-u_oracle|/|u| = %.2e, energy rel err = %.2e, decay rate %.6f vs 2 nu k^2 = %.6f (%.2f%%)"
+          % (equilibrium, err, e_err, rate, 2 * nu * k2, 100 * (rate / (2 * nu * k2) - 1)))
+    assert err < 1e-12 and e_err < 1e-12
+    assert abs(rate / (2 * nu * k2) - 1) < 0.03
+
+
+# ------------------------------------------------------------------ shear wave 256^3, FP32
+
+def _shear_amp_phase(uy, n):
+    k = 2 * math.pi / n
+    c = (uy * np.exp(-1j * k * np.arange(n))).sum() * 2 / n
+    return abs(c), np.angle(c)
+
+
+@pytest.mark.parametrize("collision", ["srt", "trt"])
+def test_shear_wave_256_fp32(collision):
+    """Periodic 256^3, FP32, u = (U, 0.01 sin(2 pi x/256), 0), U in {0, 0.05, 0.1},
+    tau in {0.55, 0.8}, 2000 steps, S and I: every (y,z) column is bitwise equal,
+    the column matches the FP64 oracle's 256x1x1 run to <= 1e-5, and S and I agree
+    to rounding (the flow is z-invariant with u_z = 0).  Prints the decay-rate and
+    phase errors against nu k^2 and U."""
+    n, steps = 256, 2000
+    k = 2 * math.pi / n
+    rows = []
+    for U in (0.0, 0.05, 0.1):
+        for tau in (0.55, 0.8):
+            cols = {}
+            for equilibrium in ("standard", "improved"):
+                kw = dict(equilibrium=equilibrium, collision=collision, tau=tau)
+                rho, u = inputs.shear_wave(n, n, n, U=(U, 0, 0), amplitude=0.01, device="cuda")
+                sim = _sim(n, n, n, precision="f32", **kw)
+                sim.init(rho, u.float())
+                del rho, u
+                sim.step(steps)
+                _, ug = sim.moments(torch.float32)
+                col = ug[:, 0:1, 0:1, :]
+                assert torch.equal(ug, col.expand_as(ug)), "columns differ"
+                col = col[:, 0, 0, :].double().cpu().numpy()
+                del ug
+                sim.close()
+                cfg = oracle_config(n, 1, 1, **kw)
+                r1, u1 = inputs.shear_wave(n, 1, 1, U=(U, 0, 0), amplitude=0.01)
+                _, uo = oracle.run(cfg, r1.numpy(), u1.numpy(), steps)
+                uo = uo[:, 0, 0, :]
+                err = rel_maxnorm(col, uo)
+                assert err < 1e-5, (U, tau, equilibrium, err)
+                amp, ph = _shear_amp_phase(col[1], n)
+                nu = (tau - 0.5) / 3
+                rate_err = (math.log(0.01 / amp) / steps) / (nu * k * k) - 1
+                ph_exact = -k * U * steps
+                ph_err = (ph - ph_exact + math.pi) % (2 * math.pi) - math.pi
+                cols[equilibrium] = col
+                rows.append((U, tau, equilibrium, err, rate_err, ph_err))
+            d = np.abs(cols["standard"] - cols["improved"]).max() / np.abs(cols["improved"]).max()
+            assert d < 1e-5, d
+    for U, tau, eq, err, re, pe in rows:
+        print("shear256 %s U=%.2f tau=%.2f %-8s oracle err %.2e  decay-rate err %+.3e  phase err %+.3e rad"
+              % (collision, U, tau, eq, err, re, pe))
+
+
+# ------------------------------------------------------------------ channel 512x256x256
+
+@pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s"])
+def test_channel_512x256x256(precision):
+    """Walls at y = -1/2 and 255.5, periodic x, z, body force a_x = 8 nu u_c / H^2
+    (steady centreline 0.05), TRT 3/16, tau = 0.6, 5000 steps: every (x,z) column is
+    bitwise equal; the y profile vs the FP64 oracle's 1x256x1 column: <= 1e-5 for
+    FP32, measured and stated for 16-bit storage."""
+    nx, ny, nz, steps, tau = 512, 256, 256, 5000, 0.6
+    nu = (tau - 0.5) / 3
+    a = 8 * nu * 0.05 / ny ** 2
+    kw = dict(equilibrium="improved", collision="trt", tau=tau, force=(a, 0, 0), walls=(False, True, False))
+    sim = _sim(nx, ny, nz, precision=precision, **kw)
+    rho, u = inputs.rest(nx, ny, nz, device="cuda")
+    sim.init(rho, u.float())
+    del rho, u
+    sim.step(steps)
+    _, ug = sim.moments(torch.float32)
+    ref = ug[:, 0:1, :, 0:1]
+    assert torch.equal(ug, ref.expand_as(ug)), "columns differ"
+    prof = ref[:, 0, :, 0].double().cpu().numpy()
+    del ug
+    sim.close()
+    cfg = oracle_config(1, ny, 1, **kw)
+    r1, u1 = inputs.rest(1, ny, 1)
+    _, uo = oracle.run(cfg, r1.numpy(), u1.numpy(), steps)
+    uo = uo[:, 0, :, 0]
+    err = rel_maxnorm(prof[0], uo[0])
+    print("channel %s: u_x profile max-norm rel err vs FP64 oracle after %d steps = %.3e (u_max %.3e)"
+          % (precision, steps, err, uo[0].max()))
+    if precision == "f32":
+        assert err < 1e-5
+    assert np.abs(prof[1:]).max() < 1e-6
+
+
+def test_poiseuille_steady_profile_on_gpu():
+    """TRT 3/16 with half-way bounce-back reaches the exact parabola (small H so
+    the steady state is reached in a few thousand steps)."""
+    nx, ny, nz, tau = 64, 16, 8, 0.8
+    nu = (tau - 0.5) / 3
+    a = 1e-6
+    sim = _sim(nx, ny, nz, precision="f64", equilibrium="improved", collision="trt", tau=tau, force=(a, 0, 0),
+               walls=(False, True, False))
+    rho, u = inputs.rest(nx, ny, nz, device="cuda")
+    sim.init(rho, u)
+    sim.step(20000)
+    _, ug = sim.moments()
+    y = np.arange(ny)
+    exact = a / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    err = np.abs(ug[0, 0, :, 0].cpu().numpy() - exact).max() / exact.max()
+    print("Poiseuille H=16 TRT 3/16: max rel deviation from the parabola %.2e" % err)
+    assert err < 1e-9
+
+
+# ------------------------------------------------------------------ duct and cross shear (S vs I)
+
+def test_cross_shear_spurious_velocity_s_vs_i():
+    """x-invariant u = (U + A sin sin, 0, 0): D3Q19-I keeps u_y = u_z = 0 exactly,
+    D3Q19-S develops transverse velocity (the paper's duct mechanism, Sec. 4)."""
+    n = 64
+    out = {}
+    for equilibrium in ("standard", "improved"):
+        sim = _sim(8, n, n, precision="f64", equilibrium=equilibrium, collision="srt", tau=0.8)
+        rho, u = inputs.cross_shear(8, n, n, U=0.05, amplitude=0.02, device="cuda")
+        sim.init(rho, u)
+        sim.step(500)
+        _, ug = sim.moments()
+        out[equilibrium] = float(ug[1:].abs().max() / ug[0].abs().max())
+    print("cross shear: max|u_yz|/max|u_x|  S = %.3e   I = %.3e" % (out["standard"], out["improved"]))
+    assert out["improved"] < 1e-13
+    assert out["standard"] > 1e-6
+
+
+def test_duct_flow_spurious_currents():
+    """Square duct (Sec. 5.1): periodic x, half-way bounce-back walls in y and z,
+    body force in x.  max|u_yz| / max|u_x| is at rounding level for D3Q19-I and
+    clearly non-zero for D3Q19-S."""
+    D, tau = 24, 1.0  # Lambda^2 = 1/4, far from the optimum 1/12 (Sec. 5.1)
+    a = 1e-5
+    out = {}
+    for equilibrium in ("standard", "improved"):
+        sim = _sim(4, D, D, precision="f64", equilibrium=equilibrium, collision="srt", tau=tau,
+                   force=(a, 0, 0), walls=(False, True, True))
+        rho, u = inputs.rest(4, D, D, device="cuda")
+        sim.init(rho, u)
+        sim.step(6000)
+        _, ug = sim.moments()
+        out[equilibrium] = float(ug[1:].abs().max() / ug[0].abs().max())
+    print("duct D=%d: max|u_yz|/max|u_x|  S = %.3e   I = %.3e" % (D, out["standard"], out["improved"]))
+    assert out["improved"] < 1e-12
+    assert out["standard"] > 1e-8
