@@ -252,18 +252,20 @@ def adjoint_ratio(args, n=128, horizon=400):
     t_adj = e0.elapsed_time(e1) * 1e-3 / reps
     sim.close()
     del lam, sim
-    # whole differentiable run
-    u0 = u.float().clone().requires_grad_(True)
-    tau = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, uT = adjoint.simulate(u0, tau, horizon, n, n, n, precision="f32")
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    L = 0.5 * ((uT.double() - tgt) ** 2).sum()
-    L.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+    # whole differentiable run (second of two, so the caching allocator holds
+    # the checkpoint and recompute buffers)
+    for _ in range(2):
+        u0 = u.float().clone().requires_grad_(True)
+        tau = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, uT = adjoint.simulate(u0, tau, horizon, n, n, n, precision="f32")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L = 0.5 * ((uT.double() - tgt) ** 2).sum()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
     return {"grid": "%d^3" % n, "horizon": horizon, "forward_step_ms": t_fwd * 1e3, "adjoint_step_ms": t_adj * 1e3,
             "adjoint_kernel_gbs": 228 * n ** 3 / t_adj / 1e9,
             "ratio_recompute_plus_adjoint_over_forward": (t_fwd + t_adj) / t_fwd,

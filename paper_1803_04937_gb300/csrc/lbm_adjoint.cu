@@ -91,12 +91,12 @@ __global__ void k_adjoint_seed(const void *grad_rho, const void *grad_u, int dty
 }
 
 // Collision constants of the adjoint step: the forward step's folded
-// constants (to recompute the collision) plus omega+-, their inverses, kappa
-// and the raw force terms F_q = 3 w_q c_q . a of the pairs.
+// constants (to recompute the collision) plus omega-, kappa and the raw force
+// terms F_q = 3 w_q c_q . a of the pairs.
 template <typename R>
 struct AdjConst {
     Relax<R> r;
-    R wp, wm, inv_wp, inv_wm, kappa;
+    R wm, kappa;
     R fraw[9];
 };
 
@@ -105,10 +105,7 @@ static inline AdjConst<R> to_adj(const CollBoth &c)
 {
     AdjConst<R> a;
     a.r = to_relax<R>(c);
-    a.wp = R(c.omega_p);
     a.wm = R(c.omega_m);
-    a.inv_wp = R(1.0 / c.omega_p);
-    a.inv_wm = R(1.0 / c.omega_m);
     a.kappa = R(c.kappa);
     for (int k = 0; k < 9; ++k) {
         const int q = 2 * k + 1;
@@ -116,6 +113,19 @@ static inline AdjConst<R> to_adj(const CollBoth &c)
                       (CX(q) * c.half_a[0] + CY(q) * c.half_a[1] + CZ(q) * c.half_a[2]));
     }
     return a;
+}
+
+template <typename R, int k>
+__device__ __forceinline__ void adj_pair(const CellEq<R, false> &e, const R mu[Q], const R fraw[9], R &cgp, R &cgm,
+                                         R &cf)
+{
+    constexpr int q = 2 * k + 1;
+    R nsym, nasym;
+    e.template neq<k>(nsym, nasym);
+    const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
+    cgp += S * nsym;
+    cgm += D * nasym;
+    cf += D * fraw[k];
 }
 
 template <typename T, typename L>
@@ -132,7 +142,7 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
     if (x < g.nx && y < g.ny) {
         Cell c(x, y, z, g);
         const int self = c.self();
-        // forward quantities of the cell at time t (rho0 = 1), and S^T: the
+        // forward populations of the cell at time t (rho0 = 1), and S^T: the
         // value that left x along c_q arrived at x + c_q (or, through a wall,
         // at the opposite slot of x).  All 38 loads are issued first.
         R f[Q], mu[Q];
@@ -144,61 +154,40 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
             long long off = wall ? (long long)OPP(q) * g.ncell + self : (long long)q * g.ncell + dst;
             mu[q] = R(lam_next[off]);
         }
-        R sf[9], df[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            sf[k] = f[2 * k + 1] + f[2 * k + 2];
-            df[k] = f[2 * k + 1] - f[2 * k + 2];
-        }
-        const R drho = f[0] + (((sf[0] + sf[1]) + (sf[2] + sf[3])) + ((sf[4] + sf[5]) + (sf[6] + sf[7])) + sf[8]);
-        R u[3] = {p.r.half_a[0], p.r.half_a[1], p.r.half_a[2]};
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int q = 2 * k + 1;
-            if (CX(q)) u[0] += R(CX(q)) * df[k];
-            if (CY(q)) u[1] += R(CY(q)) * df[k];
-            if (CZ(q)) u[2] += R(CZ(q)) * df[k];
-        }
-        const R u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
-        const R uu = u2[0] + u2[1] + u2[2];
-        const R base = drho - R(1.5) * uu;
-        const R Bf = p.r.cf * base - p.r.kf * uu;
-        const R Be[3] = {p.r.ce * base + p.r.ke * u2[0], p.r.ce * base + p.r.ke * u2[1],
-                         p.r.ce * base + p.r.ke * u2[2]};
-        // omega gradients: sum_q mu+_q (f - feq)_q = [mu0 (omega+ f0 - omega+ feq0) + sum_k S_k a1_k] / omega+,
-        // sum_q mu-_q (f - feq)_q = sum_k D_k a2_k / omega-, a1/a2 the forward step's relaxation terms.
-        R cgp = mu[0] * (p.wp * f[0] - (p.r.c0 * base + p.r.k0 * uu));
-        R cgm = R(0), cf_ = R(0);
+        const CellEq<R, false> e(f, p.r);
+        // omega gradients of this cell:
+        //   sum_q mu+_q (f - feq)_q = mu0 (f0 - feq0) + 1/2 sum_k S_k (s - 2 sym)_k
+        //   sum_q mu-_q (f - feq)_q = 1/2 sum_k D_k (d - 2 asym)_k
+        R cgp = R(0), cgm = R(0), cf_ = R(0);
+        adj_pair<R, 0>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 1>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 2>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 3>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 4>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 5>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 6>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 7>(e, mu, p.fraw, cgp, cgm, cf_);
+        adj_pair<R, 8>(e, mu, p.fraw, cgp, cgm, cf_);
+        gp_acc = -((double)(mu[0] * (f[0] - e.eq0)) + 0.5 * (double)cgp);
+        gm_acc = -0.5 * (double)cgm - 0.5 * (double)cf_;
+        // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
         R Ssum_f = R(0), Ssum_e = R(0);
         R face[3] = {R(0), R(0), R(0)}, edge[3] = {R(0), R(0), R(0)};
         R Bd[3] = {R(0), R(0), R(0)};
         R cxx = R(0), cyy = R(0), czz = R(0), cxy = R(0), cxz = R(0), cyz = R(0);
-        R S[9], D[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int q = 2 * k + 1;
-            S[k] = mu[q] + mu[q + 1];
-            D[k] = mu[q] - mu[q + 1];
-            const R cu = R(CX(q)) * u[0] + R(CY(q)) * u[1] + R(CZ(q)) * u[2];
-            R tsym, tasym;
+            const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
             const R w = WQ<R>(q);
             if (NORM2(q) == 1) {
-                const int a = CX(q) ? 0 : (CY(q) ? 1 : 2);
-                tsym = Bf + p.r.Kf * u2[a];
-                tasym = p.r.Af * cu;
-                Ssum_f += S[k];
-                face[a] += S[k];
+                Ssum_f += S;
+                face[CX(q) ? 0 : (CY(q) ? 1 : 2)] += S;
             } else {
-                const int e = CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2);
-                tsym = Be[e] + p.r.Ke * (cu * cu);
-                tasym = p.r.Ae * cu;
-                Ssum_e += S[k];
-                edge[e] += S[k];
+                Ssum_e += S;
+                edge[CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2)] += S;
             }
-            cgp += S[k] * (p.r.hp * sf[k] - tsym);
-            cgm += D[k] * (p.r.hm * df[k] - tasym);
-            cf_ += D[k] * p.fraw[k];
-            const R wD = w * D[k], wS = w * S[k];
+            const R wD = w * D, wS = w * S;
             if (CX(q)) Bd[0] += R(CX(q)) * wD;
             if (CY(q)) Bd[1] += R(CY(q)) * wD;
             if (CZ(q)) Bd[2] += R(CZ(q)) * wD;
@@ -209,27 +198,27 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ stat
             if (CX(q) * CZ(q)) cxz += R(CX(q) * CZ(q)) * wS;
             if (CY(q) * CZ(q)) cyz += R(CY(q) * CZ(q)) * wS;
         }
-        gp_acc = -(double)(cgp * p.inv_wp);
-        gm_acc = -(double)(cgm * p.inv_wm) - 0.5 * (double)cf_;
-        // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
-        const R A = p.wp * (WQ<R>(0) * mu[0] + WQ<R>(1) * Ssum_f + WQ<R>(7) * Ssum_e);
+        const R wp = p.r.wp;
+        const R A = wp * (WQ<R>(0) * mu[0] + WQ<R>(1) * Ssum_f + WQ<R>(7) * Ssum_e);
+        const R* u = e.u;
         const R cu3[3] = {cxx * u[0] + cxy * u[1] + cxz * u[2], cxy * u[0] + cyy * u[1] + cyz * u[2],
                           cxz * u[0] + cyz * u[1] + czz * u[2]};
         const R fs = face[0] + face[1] + face[2];
         R G[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const R gs = R(3) * p.wm * Bd[i] + R(9) * p.wp * cu3[i] - R(3) * A * u[i];
-            const R gd = p.wp * (mu[0] * (R(1) / R(3)) - (fs - face[i]) * (R(1) / R(6)) + edge[i] * (R(1) / R(12)));
+            const R gs = R(3) * p.wm * Bd[i] + R(9) * wp * cu3[i] - R(3) * A * u[i];
+            const R gd = wp * (mu[0] * (R(1) / R(3)) - (fs - face[i]) * (R(1) / R(6)) + edge[i] * (R(1) / R(12)));
             G[i] = gs + p.kappa * gd * u[i];
         }
-        lam[self] = L(p.r.one_m_wp * mu[0] + A);
+        lam[self] = L((R(1) - wp) * mu[0] + A);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int q = 2 * k + 1;
+            const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
             const R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
-            const R t = A - p.r.hp * S[k];
-            const R hd = p.r.hm * D[k];
+            const R t = A - p.r.hp * S;
+            const R hd = p.r.hm * D;
             lam[(long long)q * g.ncell + self] = L(mu[q] + t - hd + cg);
             lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] + t + hd - cg);
         }

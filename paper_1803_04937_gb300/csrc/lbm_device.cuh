@@ -344,22 +344,21 @@ __device__ __forceinline__ void collide(R g[Q], const Coll<R> &p)
 // ---------------------------------------------------------------- lean collision (step kernels)
 
 // Per-launch constants of the collision, folded so that a cell update needs
-// few instructions.  With P = rho0 (1, or rho when rho0 = rho), base = drho -
-// 3/2 P u^2, and omega+ times the symmetric (even) equilibrium part of a pair:
-//   faces along a:  cf base - kf u^2 + Kf u_a^2
-//   edges normal to c: ce base + ke u_c^2 + Ke (c.u)^2
-//   rest:           c0 base + k0 u^2
-// (kappa = 0: D3Q19-S; kappa = 1 adds the D3Q19-I corrections Delta), and
-// omega- times the antisymmetric part: Af (c.u) or Ae (c.u).  The factors that
-// carry P are stored for P = 1 and scaled per cell when rho0 = rho.
+// few instructions.  With P = rho0 (1, or rho when rho0 = rho) and base =
+// drho - 3/2 P u^2, the symmetric (even) equilibrium part of a pair is
+//   faces along a:     wf base - kf u^2 + Kf u_a^2
+//   edges normal to c: we base + ke u_c^2 + Ke (c.u)^2
+//   rest:              w0 base + k0 u^2
+// (kappa = 0: D3Q19-S; kappa = 1 adds the D3Q19-I corrections Delta), and the
+// antisymmetric part is A/2 (c.u) with A = 6 w P.  The factors that carry P
+// are stored for P = 1 and scaled per cell when rho0 = rho.
 template <typename R>
 struct Relax {
-    R hp, hm;        // omega+ / 2, omega- / 2
-    R one_m_wp;      // 1 - omega+
-    R c0, cf, ce;    // omega+ w_rest, omega+ w_face, omega+ w_edge
-    R k0, kf, ke;    // kappa omega+ / 6, kappa omega+ / 12, kappa omega+ / 24
-    R Kf, Ke;        // omega+ (9/2 w_face + kappa / 12), 9/2 omega+ w_edge
-    R Af, Ae;        // 3 omega- w_face, 3 omega- w_edge
+    R hp, hm, wp;    // omega+ / 2, omega- / 2, omega+
+    R w0, wf, we;    // 1/3, 1/18, 1/36
+    R k0, kf, ke;    // kappa / 6, kappa / 12, kappa / 24
+    R Kf, Ke;        // 9/2 wf + kappa / 12, 9/2 we
+    R Af, Ae;        // 6 wf, 6 we  (twice the antisymmetric coefficient)
     R half_a[3];     // a / 2
     R force[9];      // (1 - omega- / 2) F_q, q = 2k+1
 };
@@ -372,85 +371,131 @@ static inline Relax<R> to_relax(const CollBoth &c)
     Relax<R> r;
     r.hp = R(0.5 * wp);
     r.hm = R(0.5 * wm);
-    r.one_m_wp = R(1.0 - wp);
-    r.c0 = R(wp * w0);
-    r.cf = R(wp * wf);
-    r.ce = R(wp * we);
-    r.k0 = R(k * wp / 6.0);
-    r.kf = R(k * wp / 12.0);
-    r.ke = R(k * wp / 24.0);
-    r.Kf = R(wp * (4.5 * wf + k / 12.0));
-    r.Ke = R(4.5 * wp * we);
-    r.Af = R(3.0 * wm * wf);
-    r.Ae = R(3.0 * wm * we);
+    r.wp = R(wp);
+    r.w0 = R(w0);
+    r.wf = R(wf);
+    r.we = R(we);
+    r.k0 = R(k / 6.0);
+    r.kf = R(k / 12.0);
+    r.ke = R(k / 24.0);
+    r.Kf = R(4.5 * wf + k / 12.0);
+    r.Ke = R(4.5 * we);
+    r.Af = R(6.0 * wf);
+    r.Ae = R(6.0 * we);
     for (int i = 0; i < 3; ++i) r.half_a[i] = R(c.half_a[i]);
     for (int i = 0; i < 9; ++i) r.force[i] = R(c.force[i]);
     return r;
 }
 
+// Moments and symmetric-equilibrium bases of one cell, shared by the step and
+// the adjoint.  s[k], d[k]: sum and difference of pair k (q = 2k+1, q + 1).
+template <typename R, bool RHO0_IS_RHO>
+struct CellEq {
+    R s[9], d[9];
+    R u[3], u2[3], uu, P;
+    R Bf, Be[3], eq0;
+    R Kf, Ke, Af, Ae;
+
+    __device__ __forceinline__ CellEq(const R g[Q], const Relax<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            s[k] = g[2 * k + 1] + g[2 * k + 2];
+            d[k] = g[2 * k + 1] - g[2 * k + 2];
+        }
+        const R drho = g[0] + (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8]);
+        R j[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            if (CX(q) > 0) j[0] += d[k];
+            if (CX(q) < 0) j[0] -= d[k];
+            if (CY(q) > 0) j[1] += d[k];
+            if (CY(q) < 0) j[1] -= d[k];
+            if (CZ(q) > 0) j[2] += d[k];
+            if (CZ(q) < 0) j[2] -= d[k];
+        }
+        P = R(1);
+        if (RHO0_IS_RHO) {
+            P = R(1) + drho;
+            const R inv = R(1) / P;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) u[i] = (j[i] + p.half_a[i]) * inv;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) u[i] = j[i] + p.half_a[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u2[i] = u[i] * u[i];
+        uu = u2[0] + u2[1] + u2[2];
+        R k0 = p.k0, kf = p.kf, ke = p.ke;
+        Kf = p.Kf;
+        Ke = p.Ke;
+        Af = p.Af;
+        Ae = p.Ae;
+        if (RHO0_IS_RHO) {
+            k0 *= P; kf *= P; ke *= P; Kf *= P; Ke *= P; Af *= P; Ae *= P;
+        }
+        const R base = drho - R(1.5) * P * uu;
+        Bf = p.wf * base - kf * uu;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Be[i] = p.we * base + ke * u2[i];
+        eq0 = p.w0 * base + k0 * uu;
+    }
+
+    // Non-equilibrium parts of pair k: s - 2 sym and d - 2 asym, each formed
+    // by one fused multiply-add so that only the small result is rounded.
+    template <int k>
+    __device__ __forceinline__ void neq(R &nsym, R &nasym) const
+    {
+        constexpr int q = 2 * k + 1;
+        const R cu = R(CX(q)) * u[0] + R(CY(q)) * u[1] + R(CZ(q)) * u[2];
+        R sym, A;
+        if (NORM2(q) == 1) {
+            const int a = CX(q) ? 0 : (CY(q) ? 1 : 2);
+            sym = Bf + Kf * u2[a];
+            A = Af;
+        } else {
+            const int c = CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2);
+            sym = Be[c] + Ke * (cu * cu);
+            A = Ae;
+        }
+        nsym = fma(R(-2), sym, s[k]);
+        nasym = fma(-A, cu, d[k]);
+    }
+};
+
 // One collision (Eq. 15, or its TRT split) of the shifted populations g in
-// place.  Same result as the textbook form g - omega+ (g+ - geq+) -
-// omega- (g- - geq-) + (1 - omega-/2) F up to rounding order.
+// place: g -/+ (omega+/2)(s - 2 sym) -/+ (omega-/2)(d - 2 asym) +/- (1 -
+// omega-/2) F for the two members of each pair; the same result as the
+// textbook form g - omega+ (g+ - geq+) - omega- (g- - geq-) + (1 - omega-/2) F
+// up to rounding order.
+template <typename R, bool RHO0_IS_RHO, int k>
+__device__ __forceinline__ void relax_pair(R g[Q], const CellEq<R, RHO0_IS_RHO> &e, const Relax<R> &p)
+{
+    constexpr int q = 2 * k + 1;
+    R nsym, nasym;
+    e.template neq<k>(nsym, nasym);
+    const R a1 = p.hp * nsym;
+    const R b = fma(p.hm, nasym, -p.force[k]);
+    g[q] = (g[q] - a1) - b;
+    g[q + 1] = (g[q + 1] - a1) + b;
+}
+
 template <typename R, bool RHO0_IS_RHO>
 __device__ __forceinline__ void collide_lean(R g[Q], const Relax<R> &p)
 {
-    R s[9], d[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        s[k] = g[2 * k + 1] + g[2 * k + 2];
-        d[k] = g[2 * k + 1] - g[2 * k + 2];
-    }
-    const R drho = g[0] + (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8]);
-    R j[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int q = 2 * k + 1;
-        if (CX(q) > 0) j[0] += d[k];
-        if (CX(q) < 0) j[0] -= d[k];
-        if (CY(q) > 0) j[1] += d[k];
-        if (CY(q) < 0) j[1] -= d[k];
-        if (CZ(q) > 0) j[2] += d[k];
-        if (CZ(q) < 0) j[2] -= d[k];
-    }
-    R P = R(1), u[3];
-    if (RHO0_IS_RHO) {
-        P = R(1) + drho;
-        const R inv = R(1) / P;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) u[i] = (j[i] + p.half_a[i]) * inv;
-    } else {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) u[i] = j[i] + p.half_a[i];
-    }
-    const R u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
-    const R uu = u2[0] + u2[1] + u2[2];
-    R k0 = p.k0, kf = p.kf, ke = p.ke, Kf = p.Kf, Ke = p.Ke, Af = p.Af, Ae = p.Ae;
-    if (RHO0_IS_RHO) {
-        k0 *= P; kf *= P; ke *= P; Kf *= P; Ke *= P; Af *= P; Ae *= P;
-    }
-    const R base = drho - R(1.5) * P * uu;
-    const R Bf = p.cf * base - kf * uu;
-    const R Be[3] = {p.ce * base + ke * u2[0], p.ce * base + ke * u2[1], p.ce * base + ke * u2[2]};
-    g[0] = p.one_m_wp * g[0] + (p.c0 * base + k0 * uu);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int q = 2 * k + 1;
-        const R cu = R(CX(q)) * u[0] + R(CY(q)) * u[1] + R(CZ(q)) * u[2];
-        R tsym, tasym;
-        if (NORM2(q) == 1) {
-            const int a = CX(q) ? 0 : (CY(q) ? 1 : 2);
-            tsym = Bf + Kf * u2[a];
-            tasym = Af * cu;
-        } else {
-            const int c = CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2);
-            tsym = Be[c] + Ke * (cu * cu);
-            tasym = Ae * cu;
-        }
-        const R a1 = p.hp * s[k] - tsym;
-        const R b = (p.hm * d[k] - tasym) - p.force[k];
-        g[q] = (g[q] - a1) - b;
-        g[q + 1] = (g[q + 1] - a1) + b;
-    }
+    const CellEq<R, RHO0_IS_RHO> e(g, p);
+    g[0] = fma(-p.wp, g[0] - e.eq0, g[0]);
+    relax_pair<R, RHO0_IS_RHO, 0>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 1>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 2>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 3>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 4>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 5>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 6>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 7>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, 8>(g, e, p);
 }
 
 // Shifted equilibrium geq_q = feq_q(rho, u) - w_q for all q (lbm_init).

@@ -90,60 +90,53 @@ template <> struct Pair<__nv_bfloat16> {
     }
 };
 
-// A/B pull step, two cells (x0, x0 + 1) per thread, x0 even, nx even.
+// Pair-wise gather for two cells (x0, x0 + 1), x0 even, nx even, of the
+// populations that stream into them.  SWAP = false: A/B layout (plane q at
+// x - c_q, through a wall plane qbar of the own cell); SWAP = true: AA odd
+// layout (plane qbar at x - c_q, through a wall plane q of the own cell).
 // blockDim.x is a multiple of 32, so a warp never spans two lattice rows and
-// lane 0 of a warp starts a 64-cell segment of its row.
-template <typename T, bool RHO0>
-__global__ void __launch_bounds__(256) k_step_ab2(const T *__restrict__ src, T *__restrict__ dst, Geo g,
-                                                  Relax<typename Storage<T>::R> p)
+// lane 0 of a warp starts a 64-cell segment of its row.  Inactive lanes
+// (x0 >= nx) read a valid pair and take part in the shuffles.
+template <bool SWAP, typename T, typename R>
+__device__ __forceinline__ void gather2(const T *grid, const Cell &c, const Geo &g, int lane, int x0, bool active,
+                                        int own, R f0[Q], R f1[Q])
 {
-    using R = typename Storage<T>::R;
-    const int lane = threadIdx.x & 31;
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (y >= g.ny) return;  // uniform across the warp
-    const bool active = x0 < g.nx;
-    const int xs = active ? x0 : 0;  // inactive lanes read a valid pair and take part in the shuffles
-    Cell c(xs, y, z, g);
-    const int own = z * c.nxy + y * c.nx;
+    const int xs = active ? x0 : 0;
     // Phase 1: issue every load before any shuffle (shuffles wait for their
     // operand, and interleaving them with the loads would serialise memory
     // latencies).  lo/hi: the own pair of the source row (or, through a y/z
-    // wall, the own cell's opposite-slot pair); e: the element beyond the
-    // warp's edge for the +-x populations, loaded only by the edge lane.
+    // wall, the own cell's reflected pair); e: the element beyond the warp's
+    // edge for the +-x populations, loaded only by the edge lane.
     R lo[Q], hi[Q], e[Q];
     bool wyz[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q), cy = CY(q), cz = CZ(q);
-        const int ys = cy == 0 ? y : (cy > 0 ? c.ym : c.yp);
-        const int zs = cz == 0 ? z : (cz > 0 ? c.zm : c.zp);
+        const int ys = cy == 0 ? c.y : (cy > 0 ? c.ym : c.yp);
+        const int zs = cz == 0 ? c.z : (cz > 0 ? c.zm : c.zp);
         bool w = false;
         if (cy > 0) w |= c.bym;
         if (cy < 0) w |= c.byp;
         if (cz > 0) w |= c.bzm;
         if (cz < 0) w |= c.bzp;
         wyz[q] = w;
-        const T *plane = src + (long long)q * g.ncell;
-        const T *oplane = src + (long long)OPP(q) * g.ncell;
+        const T *plane = grid + (long long)(SWAP ? OPP(q) : q) * g.ncell;   // streamed value
+        const T *bplane = grid + (long long)(SWAP ? q : OPP(q)) * g.ncell;  // bounced value
         const int srow = zs * c.nxy + ys * c.nx;
-        Pair<T>::load(w ? oplane + own + xs : plane + srow + xs, lo[q], hi[q]);
+        Pair<T>::load(w ? bplane + own + xs : plane + srow + xs, lo[q], hi[q]);
         e[q] = R(0);
         if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
             const bool need = lane == 0 && active && !w;
-            const T *a = (x0 == 0 && g.wall_x) ? oplane + own + xs
-                                                : plane + srow + (xs == 0 ? g.nx - 1 : xs - 1);
+            const T *a = (xs == 0 && g.wall_x) ? bplane + own + xs : plane + srow + (xs == 0 ? g.nx - 1 : xs - 1);
             if (need) e[q] = Storage<T>::load(a);
         } else if (cx < 0) {  // pull from x + 1: the last lane of a segment needs element x0 + 2
             const bool need = (lane == 31 || xs + 2 >= g.nx) && active && !w;
-            const T *a = (xs + 2 >= g.nx && g.wall_x) ? oplane + own + xs + 1
+            const T *a = (xs + 2 >= g.nx && g.wall_x) ? bplane + own + xs + 1
                                                        : plane + srow + (xs + 2 >= g.nx ? 0 : xs + 2);
             if (need) e[q] = Storage<T>::load(a);
         }
     }
     // Phase 2: assemble the shifted pairs.
-    R f0[Q], f1[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q);
@@ -162,11 +155,110 @@ __global__ void __launch_bounds__(256) k_step_ab2(const T *__restrict__ src, T *
             f1[q] = wyz[q] ? hi[q] : right;
         }
     }
+}
+
+// A/B pull step, two cells (x0, x0 + 1) per thread.
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(256) k_step_ab2(const T *__restrict__ src, T *__restrict__ dst, Geo g,
+                                                  Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    Cell c(active ? x0 : 0, y, z, g);
+    const int own = z * c.nxy + y * c.nx;
+    R f0[Q], f1[Q];
+    gather2<false>(src, c, g, lane, x0, active, own, f0, f1);
     if (!active) return;
     collide_lean<R, RHO0>(f0, p);
     collide_lean<R, RHO0>(f1, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Pair<T>::store(dst + (long long)q * g.ncell + own + x0, f0[q], f1[q]);
+}
+
+// AA odd step, two cells per thread: gather plane qbar from x - c_q (pairs,
+// as above), collide, and write plane q at x + c_q.  A +-x shifted write is
+// assembled into the aligned pair (x0, x0 + 1) of the target row from the own
+// values and the neighbouring lane's (warp shuffle); the element that belongs
+// to the neighbouring warp's pair is written by the edge lane as a scalar.
+// Through a wall the value goes to plane qbar of the own cell.  Every
+// location is written by exactly one thread, as in the one-cell kernel.
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(256, 2) k_step_aa_odd2(T *grid, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    Cell c(active ? x0 : 0, y, z, g);
+    const int own = z * c.nxy + y * c.nx;
+    R f0[Q], f1[Q];
+    gather2<true>(grid, c, g, lane, x0, active, own, f0, f1);
+    if (active) {
+        collide_lean<R, RHO0>(f0, p);
+        collide_lean<R, RHO0>(f1, p);
+    }
+    const bool last = lane == 31 || x0 + 2 >= g.nx;  // right edge of this warp's segment
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q), cy = CY(q), cz = CZ(q);
+        const int yt = cy == 0 ? y : (cy > 0 ? c.yp : c.ym);
+        const int zt = cz == 0 ? z : (cz > 0 ? c.zp : c.zm);
+        bool w = false;
+        if (cy > 0) w |= c.byp;
+        if (cy < 0) w |= c.bym;
+        if (cz > 0) w |= c.bzp;
+        if (cz < 0) w |= c.bzm;
+        T *plane = grid + (long long)q * g.ncell;        // streamed value
+        T *bplane = grid + (long long)OPP(q) * g.ncell;  // bounced value
+        const int trow = zt * c.nxy + yt * c.nx;
+        if (cx == 0) {
+            if (active) Pair<T>::store(w ? bplane + own + x0 : plane + trow + x0, f0[q], f1[q]);
+        } else if (cx > 0) {
+            // element x0 of the target row receives cell x0 - 1, element x0 + 1 cell x0
+            const R left = __shfl_up_sync(0xffffffffu, f1[q], 1);
+            if (!active) continue;
+            if (w) {
+                Pair<T>::store(bplane + own + x0, f0[q], f1[q]);
+                continue;
+            }
+            if (lane == 0)
+                Storage<T>::store(plane + trow + x0 + 1, f0[q]);
+            else
+                Pair<T>::store(plane + trow + x0, left, f0[q]);
+            if (last) {  // cell x0 + 1 goes to x0 + 2: the next segment, the periodic image, or a wall
+                if (x0 + 2 >= g.nx && g.wall_x)
+                    Storage<T>::store(bplane + own + x0 + 1, f1[q]);
+                else
+                    Storage<T>::store(plane + trow + (x0 + 2 >= g.nx ? 0 : x0 + 2), f1[q]);
+            }
+        } else {
+            // element x0 of the target row receives cell x0 + 1, element x0 + 1 cell x0 + 2
+            const R right = __shfl_down_sync(0xffffffffu, f0[q], 1);
+            if (!active) continue;
+            if (w) {
+                Pair<T>::store(bplane + own + x0, f0[q], f1[q]);
+                continue;
+            }
+            if (last)
+                Storage<T>::store(plane + trow + x0, f1[q]);
+            else
+                Pair<T>::store(plane + trow + x0, f1[q], right);
+            if (lane == 0) {  // cell x0 goes to x0 - 1: the previous segment, the periodic image, or a wall
+                if (x0 == 0 && g.wall_x)
+                    Storage<T>::store(bplane + own + x0, f0[q]);
+                else
+                    Storage<T>::store(plane + trow + (x0 == 0 ? g.nx - 1 : x0 - 1), f0[q]);
+            }
+        }
+    }
 }
 
 // AA in-place steps.  Even: own cell only (read q, write qbar).  Odd: read
@@ -234,9 +326,10 @@ static cudaError_t step_t(int kind, const void *src, void *dst, const Geo &g, co
         else
             k_step_aa<T, 0, RHO0><<<grid, block, 0, stream>>>((T *)dst, g, p);
     } else {
-        // the odd AA step writes to x + c_q: one cell per thread
-        dim3 grid1((g.nx + s.bx - 1) / s.bx, (g.ny + s.by - 1) / s.by, g.nz);
-        k_step_aa<T, 1, RHO0><<<grid1, block, 0, stream>>>((T *)dst, g, p);
+        if (pairs)
+            k_step_aa_odd2<T, RHO0><<<grid, block, 0, stream>>>((T *)dst, g, p);
+        else
+            k_step_aa<T, 1, RHO0><<<grid, block, 0, stream>>>((T *)dst, g, p);
     }
     return cudaGetLastError();
 }
