@@ -48,6 +48,10 @@ def parse_args(argv=None):
     p.add_argument("--equilibrium", choices=["standard", "improved"], default="improved")
     p.add_argument("--tau", type=float, default=0.8)
     p.add_argument("--block", type=str, default=None, help="step kernel block 'bx,by'")
+    p.add_argument("--cells-x", type=int, choices=[1, 2], default=None,
+                   help="step kernel cells per thread along x (default: library's choice)")
+    p.add_argument("--only-adjoint", action="store_true",
+                   help="time only the adjoint workload (128^3) and print its figures")
     p.add_argument("--no-extras", action="store_true", help="main line only (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args(argv)
@@ -196,7 +200,7 @@ def make_sim(args, n, precision=None, pattern=None, collision=None, equilibrium=
     block = tuple(int(x) for x in args.block.split(",")) if args.block else None
     sim = Simulation(n, n, n, equilibrium=equilibrium or args.equilibrium, collision=collision or args.collision,
                      tau=args.tau, precision=precision or args.precision, pattern=pattern or args.pattern,
-                     device=device, block=block)
+                     device=device, block=block, cells_x=args.cells_x)
     rho, u = shear_workload(n, n, n, device)
     sim.init(rho, u.float() if (precision or args.precision) != "f64" else u)
     del rho, u
@@ -453,6 +457,9 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_adjoint:
+        print(json.dumps({"adjoint": adjoint_ratio(args)}), flush=True)
+        return 0
     return run_native(args)
 
 
