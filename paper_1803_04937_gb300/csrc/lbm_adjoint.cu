@@ -129,7 +129,7 @@ __device__ __forceinline__ void adj_pair(const CellEq<R, false> &e, const R mu[Q
 }
 
 template <typename T, typename L>
-__global__ void __launch_bounds__(256) k_adjoint_step(const T *__restrict__ state, const L *__restrict__ lam_next,
+__global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 : 4) k_adjoint_step(const T *__restrict__ state, const L *__restrict__ lam_next,
                                                       L *__restrict__ lam, double *partial, Geo g,
                                                       AdjConst<typename Storage<T>::R> p)
 {

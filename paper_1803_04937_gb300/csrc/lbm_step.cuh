@@ -1,0 +1,446 @@
+// Fused stream + collide time step (Eq. 15; D3Q19-S / D3Q19-I equilibria;
+// SRT / TRT; periodic or half-way bounce-back; Buick-Greated force): kernel
+// templates, instantiated per storage precision in lbm_step_<prec>.cu.
+//
+// Each thread gathers the populations that stream into its cell(s), collides
+// them in registers (FP32, or FP64 for FP64 storage) and stores the
+// post-collision values.  Structure-of-arrays storage gives coalesced accesses
+// along x for every population.  Algorithmic traffic: 19 loads + 19 stores
+// per cell.
+//
+// Address arithmetic is kept to one 32-bit index per access: the base pointer
+// of each population plane comes from the kernel parameters (a table of 19
+// pointers) and the nine source/target row offsets (y +- 1, z +- 1, wrapped)
+// are formed once per thread.  WALLS = false compiles the periodic lattice
+// without any bounce-back logic.
+//
+// Two thread mappings:
+//  - one cell per thread (any nx): scalar loads; the +-x populations are read
+//    one element off alignment, which L1/L2 absorb without extra DRAM traffic.
+//  - two neighbouring cells per thread (nx even): every population is read
+//    and written as an aligned pair (half2 / bfloat162 / float2 / double2);
+//    a +-x shifted pair is assembled from the own pair and one element of the
+//    neighbouring lane's pair (warp shuffle), with one scalar access at the
+//    warp's edge.  Halves the load/store instructions and the index work.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_launch.h"
+
+namespace lbm {
+
+template <typename T> struct Planes {
+    T *p[Q];
+};
+
+template <typename T>
+static inline Planes<T> planes_of(void *base, long long ncell)
+{
+    Planes<T> r;
+    for (int q = 0; q < Q; ++q) r.p[q] = (T *)base + (long long)q * ncell;
+    return r;
+}
+
+// Per-thread lattice geometry: wrapped neighbour coordinates, the nine row
+// offsets of the rows y + dy, z + dz (dy, dz in {-1, 0, 1}) and, with walls,
+// the wall flags of the six faces of the cell(s).
+template <bool WALLS>
+struct Site {
+    int x, xm, xp;      // x and its wrapped neighbours (first cell of the thread)
+    int row[3][3];      // row[dy + 1][dz + 1] = ((z + dz) ny + (y + dy)) nx, wrapped
+    int own;            // row[1][1]
+    bool bxm, bxp, bym, byp, bzm, bzp;
+
+    __device__ __forceinline__ Site(int x_, int y, int z, int span, const Geo &g)
+    {
+        x = x_;
+        xm = x == 0 ? g.nx - 1 : x - 1;
+        xp = x + span >= g.nx ? x + span - g.nx : x + span;  // first cell after the thread's span
+        const int ym = y == 0 ? g.ny - 1 : y - 1;
+        const int yp = y == g.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? g.nz - 1 : z - 1;
+        const int zp = z == g.nz - 1 ? 0 : z + 1;
+        const int nxy = g.nx * g.ny;
+        const int ys[3] = {ym, y, yp}, zs[3] = {zm, z, zp};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) row[a][b] = zs[b] * nxy + ys[a] * g.nx;
+        own = row[1][1];
+        if (WALLS) {
+            bxm = g.wall_x && x == 0;
+            bxp = g.wall_x && x + span >= g.nx;
+            bym = g.wall_y && y == 0;
+            byp = g.wall_y && y == g.ny - 1;
+            bzm = g.wall_z && z == 0;
+            bzp = g.wall_z && z == g.nz - 1;
+        } else {
+            bxm = bxp = bym = byp = bzm = bzp = false;
+        }
+    }
+
+    // Does the link from the cell along s * c_q cross a y/z wall?
+    template <int S>
+    __device__ __forceinline__ bool wall_yz(int q) const
+    {
+        if (!WALLS) return false;
+        const int cy = S * CY(q), cz = S * CZ(q);
+        bool w = false;
+        if (cy > 0) w |= byp;
+        if (cy < 0) w |= bym;
+        if (cz > 0) w |= bzp;
+        if (cz < 0) w |= bzm;
+        return w;
+    }
+    template <int S>
+    __device__ __forceinline__ int row_along(int q) const
+    {
+        return row[S * CY(q) + 1][S * CZ(q) + 1];
+    }
+};
+
+// ---------------------------------------------------------------- pairs
+
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    static __device__ __forceinline__ void load(const float *p, float &a, float &b)
+    {
+        float2 v = *reinterpret_cast<const float2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void store(float *p, float a, float b)
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+};
+template <> struct Pair<double> {
+    static __device__ __forceinline__ void load(const double *p, double &a, double &b)
+    {
+        double2 v = *reinterpret_cast<const double2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void store(double *p, double a, double b)
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+    }
+};
+template <> struct Pair<__half> {
+    static __device__ __forceinline__ void load(const __half *p, float &a, float &b)
+    {
+        __half2 v = *reinterpret_cast<const __half2 *>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    static __device__ __forceinline__ void store(__half *p, float a, float b)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float &a, float &b)
+    {
+        __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float a, float b)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// ---------------------------------------------------------------- one cell per thread
+
+// Gather of the populations streaming into one cell.  SWAP = false: A/B
+// layout (plane q at x - c_q; through a wall, plane qbar of the own cell);
+// SWAP = true: AA odd layout (plane qbar at x - c_q; through a wall, plane q
+// of the own cell).
+template <bool SWAP, bool WALLS, typename T, typename R>
+__device__ __forceinline__ void gather1(const Planes<T> &P, const Site<WALLS> &s, R f[Q])
+{
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const int xs = cx == 0 ? s.x : (cx > 0 ? s.xm : s.xp);
+        bool w = s.template wall_yz<-1>(q);
+        if (WALLS) {
+            if (cx > 0) w |= s.bxm;
+            if (cx < 0) w |= s.bxp;
+        }
+        const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
+        const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
+        const T *a = w ? bnc + s.own + s.x : src + s.template row_along<-1>(q) + xs;
+        f[q] = Storage<T>::load(a);
+    }
+}
+
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const Site<WALLS> s(x, y, z, 1, g);
+    R f[Q];
+    gather1<false>(src, s, f);
+    collide_lean<R, RHO0>(f, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Storage<T>::store(dst.p[q] + s.own + x, f[q]);
+}
+
+// AA even step: own cell only (read plane q, write plane qbar).
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int own = (z * g.ny + y) * g.nx + x;
+    R f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = Storage<T>::load(P.p[q] + own);
+    collide_lean<R, RHO0>(f, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Storage<T>::store(P.p[OPP(q)] + own, f[q]);
+}
+
+// AA odd step: read plane qbar at x - c_q, write plane q at x + c_q (through
+// a wall: read plane q / write plane qbar of the own cell).  Every location is
+// read and written by exactly one thread.
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(256) k_aa_odd1(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const Site<WALLS> s(x, y, z, 1, g);
+    R f[Q];
+    gather1<true>(P, s, f);
+    collide_lean<R, RHO0>(f, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const int xt = cx == 0 ? x : (cx > 0 ? s.xp : s.xm);
+        bool w = s.template wall_yz<1>(q);
+        if (WALLS) {
+            if (cx > 0) w |= s.bxp;
+            if (cx < 0) w |= s.bxm;
+        }
+        T *a = w ? P.p[OPP(q)] + s.own + x : P.p[q] + s.template row_along<1>(q) + xt;
+        Storage<T>::store(a, f[q]);
+    }
+}
+
+// ---------------------------------------------------------------- two cells per thread
+
+// Pair-wise gather for the cells (x0, x0 + 1), x0 even, nx even (layouts as
+// in gather1).  blockDim.x is a multiple of 32, so a warp never spans two
+// lattice rows and lane 0 of a warp starts a 64-cell segment of its row.
+// Inactive lanes (x0 >= nx) read a valid pair and take part in the shuffles.
+template <bool SWAP, bool WALLS, typename T, typename R>
+__device__ __forceinline__ void gather2(const Planes<T> &P, const Site<WALLS> &s, const Geo &g, int lane,
+                                        bool active, R f0[Q], R f1[Q])
+{
+    const int x0 = s.x;
+    const bool last = lane == 31 || x0 + 2 >= g.nx;
+    // Phase 1: issue every load before any shuffle.  lo/hi: the own pair of
+    // the source row (or, through a y/z wall, the own cell's reflected pair);
+    // e: the element beyond the segment's edge for the +-x populations.
+    R lo[Q], hi[Q], e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const bool w = s.template wall_yz<-1>(q);
+        const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
+        const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
+        const int srow = s.template row_along<-1>(q);
+        Pair<T>::load(w ? bnc + s.own + x0 : src + srow + x0, lo[q], hi[q]);
+        e[q] = R(0);
+        if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
+            const T *a = (WALLS && s.bxm) ? bnc + s.own + x0 : src + srow + s.xm;
+            if (lane == 0 && active && !w) e[q] = Storage<T>::load(a);
+        } else if (cx < 0) {  // pull from x + 1: the segment's last lane needs element x0 + 2
+            const T *a = (WALLS && s.bxp) ? bnc + s.own + x0 + 1 : src + srow + s.xp;
+            if (last && active && !w) e[q] = Storage<T>::load(a);
+        }
+    }
+    // Phase 2: assemble the shifted pairs.
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const bool w = s.template wall_yz<-1>(q);
+        if (cx == 0) {
+            f0[q] = lo[q];
+            f1[q] = hi[q];
+        } else if (cx > 0) {
+            R left = __shfl_up_sync(0xffffffffu, hi[q], 1);
+            if (lane == 0) left = e[q];
+            f0[q] = w ? lo[q] : left;
+            f1[q] = w ? hi[q] : lo[q];
+        } else {
+            R right = __shfl_down_sync(0xffffffffu, lo[q], 1);
+            if (last) right = e[q];
+            f0[q] = w ? lo[q] : hi[q];
+            f1[q] = w ? hi[q] : right;
+        }
+    }
+}
+
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(256) k_ab2(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    const Site<WALLS> s(active ? x0 : 0, y, z, 2, g);
+    R f0[Q], f1[Q];
+    gather2<false>(src, s, g, lane, active, f0, f1);
+    if (!active) return;
+    collide_lean<R, RHO0>(f0, p);
+    collide_lean<R, RHO0>(f1, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Pair<T>::store(dst.p[q] + s.own + x0, f0[q], f1[q]);
+}
+
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(256) k_aa_even2(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= g.nx || y >= g.ny) return;
+    const int own = (z * g.ny + y) * g.nx + x0;
+    R f0[Q], f1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Pair<T>::load(P.p[q] + own, f0[q], f1[q]);
+    collide_lean<R, RHO0>(f0, p);
+    collide_lean<R, RHO0>(f1, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Pair<T>::store(P.p[OPP(q)] + own, f0[q], f1[q]);
+}
+
+// AA odd step, two cells per thread: gather plane qbar from x - c_q (pairs),
+// collide, and write plane q at x + c_q.  A +-x shifted write is assembled
+// into the aligned pair (x0, x0 + 1) of the target row from the own values and
+// the neighbouring lane's (warp shuffle); the element that belongs to the
+// neighbouring segment is written by the edge lane as a scalar.  Through a
+// wall the value goes to plane qbar of the own cell.  Every location is
+// written by exactly one thread, as in the one-cell kernel.
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(256, 2) k_aa_odd2(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
+{
+    using R = typename Storage<T>::R;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    const Site<WALLS> s(active ? x0 : 0, y, z, 2, g);
+    R f0[Q], f1[Q];
+    gather2<true>(P, s, g, lane, active, f0, f1);
+    if (active) {
+        collide_lean<R, RHO0>(f0, p);
+        collide_lean<R, RHO0>(f1, p);
+    }
+    const bool last = lane == 31 || x0 + 2 >= g.nx;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const bool w = s.template wall_yz<1>(q);
+        T *dst = P.p[q];
+        T *bnc = P.p[OPP(q)];
+        const int trow = s.template row_along<1>(q);
+        if (cx == 0) {
+            if (active) Pair<T>::store(w ? bnc + s.own + x0 : dst + trow + x0, f0[q], f1[q]);
+        } else if (cx > 0) {
+            // element x0 of the target row receives cell x0 - 1, element x0 + 1 cell x0
+            const R left = __shfl_up_sync(0xffffffffu, f1[q], 1);
+            if (!active) continue;
+            if (w) {
+                Pair<T>::store(bnc + s.own + x0, f0[q], f1[q]);
+                continue;
+            }
+            if (lane == 0)
+                Storage<T>::store(dst + trow + x0 + 1, f0[q]);
+            else
+                Pair<T>::store(dst + trow + x0, left, f0[q]);
+            if (last)  // cell x0 + 1 goes to x0 + 2: the next segment, the periodic image, or a wall
+                Storage<T>::store((WALLS && s.bxp) ? bnc + s.own + x0 + 1 : dst + trow + s.xp, f1[q]);
+        } else {
+            // element x0 of the target row receives cell x0 + 1, element x0 + 1 cell x0 + 2
+            const R right = __shfl_down_sync(0xffffffffu, f0[q], 1);
+            if (!active) continue;
+            if (w) {
+                Pair<T>::store(bnc + s.own + x0, f0[q], f1[q]);
+                continue;
+            }
+            if (last)
+                Storage<T>::store(dst + trow + x0, f1[q]);
+            else
+                Pair<T>::store(dst + trow + x0, f1[q], right);
+            if (lane == 0)  // cell x0 goes to x0 - 1: the previous segment, the periodic image, or a wall
+                Storage<T>::store((WALLS && s.bxm) ? bnc + s.own + x0 : dst + trow + s.xm, f0[q]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- dispatch
+
+template <typename T, bool RHO0, bool WALLS>
+static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const CollBoth &cb, LaunchShape ls,
+                          cudaStream_t stream)
+{
+    using R = typename Storage<T>::R;
+    const Relax<R> p = to_relax<R>(cb);
+    const dim3 block(ls.bx, ls.by, 1);
+    const bool pairs = ls.cells_x == 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
+    const int span = pairs ? 2 * ls.bx : ls.bx;
+    const dim3 grid((g.nx + span - 1) / span, (g.ny + ls.by - 1) / ls.by, g.nz);
+    const Planes<T> D = planes_of<T>(dst, g.ncell);
+    if (kind == 0) {
+        const Planes<T> S = planes_of<T>(src, g.ncell);
+        if (pairs)
+            k_ab2<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
+        else
+            k_ab1<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
+    } else if (kind == 1) {
+        if (pairs)
+            k_aa_even2<T, RHO0><<<grid, block, 0, stream>>>(D, g, p);
+        else
+            k_aa_even1<T, RHO0><<<grid, block, 0, stream>>>(D, g, p);
+    } else {
+        if (pairs)
+            k_aa_odd2<T, RHO0, WALLS><<<grid, block, 0, stream>>>(D, g, p);
+        else
+            k_aa_odd1<T, RHO0, WALLS><<<grid, block, 0, stream>>>(D, g, p);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t step_any(int kind, void *src, void *dst, const Geo &g, const CollBoth &cb, LaunchShape s,
+                            cudaStream_t stream)
+{
+    const bool walls = g.wall_x || g.wall_y || g.wall_z;
+    if (cb.rho0_is_rho)
+        return walls ? step_t<T, true, true>(kind, src, dst, g, cb, s, stream)
+                     : step_t<T, true, false>(kind, src, dst, g, cb, s, stream);
+    return walls ? step_t<T, false, true>(kind, src, dst, g, cb, s, stream)
+                 : step_t<T, false, false>(kind, src, dst, g, cb, s, stream);
+}
+
+}  // namespace lbm
