@@ -156,7 +156,7 @@ def read_traffic(kernel_key):
     if not e:
         return None, None
     src = b""
-    for f in ("lbm_device.cuh", "lbm_step.cu"):
+    for f in ("lbm_device.cuh", "lbm_step.cuh"):
         src += open(os.path.join(ROOT, "paper_1803_04937_gb300", "csrc", f), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     if e.get("source_sha") != sha:
@@ -406,7 +406,11 @@ def run_native(args):
     per_launch = t_local / args.steps
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LUP[args.precision] * cells / per_launch / 1e9
-    kname = "k_step_%s<%s>" % (args.pattern, args.precision)
+    cx = args.cells_x or (2 if args.precision in ("f16s", "bf16s") else 1)
+    if args.pattern == "ab":
+        kname = "k_ab%d<%s>" % (cx, args.precision)
+    else:
+        kname = "k_aa_even%d+k_aa_odd%d<%s>" % (cx, cx, args.precision)
     traffic_per_lup, _ = read_traffic(kname)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
