@@ -380,8 +380,13 @@ static inline Relax<R> to_relax(const CollBoth &c)
     r.ke = R(k / 24.0);
     r.Kf = R(4.5 * wf + k / 12.0);
     r.Ke = R(4.5 * we);
-    r.Af = R(6.0 * wf);
-    r.Ae = R(6.0 * we);
+    // The equilibrium's first moment is (Af + 4 Ae) u per axis; with the
+    // weights rounded to R it would be u (1 + eps), and the antisymmetric
+    // relaxation would then grow the momentum by omega- eps every step (2000
+    // FP32 steps: ~1e-4).  Af is chosen so that Af + 4 Ae = 1 exactly in R
+    // (1 - 4 Ae is exact by Sterbenz's lemma).
+    r.Ae = R(1.0 / 6.0);
+    r.Af = R(1) - R(4) * r.Ae;
     for (int i = 0; i < 3; ++i) r.half_a[i] = R(c.half_a[i]);
     for (int i = 0; i < 9; ++i) r.force[i] = R(c.force[i]);
     return r;

@@ -174,3 +174,41 @@ def test_zero_steps_returns_initial_fields():
         sim.step(0)
         r, uu = sim.moments()
         assert torch.allclose(r.cpu(), rho, atol=1e-15) and torch.allclose(uu.cpu(), u, atol=1e-15)
+
+
+@pytest.mark.parametrize("collision,tau", [("srt", 0.55), ("srt", 0.8), ("trt", 0.6)])
+@pytest.mark.parametrize("precision,tol", [("f32", 2e-6), ("f64", 1e-13)])
+def test_uniform_flow_keeps_its_momentum(collision, tau, precision, tol):
+    """A uniform flow is a fixed point of Eq. 15; in working precision the
+    equilibrium's first moment must be exactly u, or the antisymmetric
+    relaxation drifts the momentum by a constant factor every step."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    n = 16
+    U = (0.1, -0.05, 0.02)
+    u = torch.zeros((3, n, n, n), dtype=torch.float64)
+    for i in range(3):
+        u[i] = U[i]
+    sim = Simulation(n, n, n, precision=precision, collision=collision, tau=tau)
+    sim.init(torch.ones((n, n, n), dtype=torch.float64).cuda(), u.cuda())
+    sim.step(2000)
+    _, ug = sim.moments()
+    err = float((ug.cpu() - u).abs().max() / 0.1)
+    print("uniform flow %s %s tau=%.2f: max|u - U|/|U_x| after 2000 steps = %.2e" % (precision, collision, tau, err))
+    assert err < tol
+
+
+def test_fp32_global_momentum_drift():
+    """Global momentum of a random periodic flow in FP32 storage over 1000 steps
+    (FP64 reduction): conserved to rounding, no systematic drift."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    shape = (24, 24, 24)
+    rho, u = random_fields(shape, seed=77, amp=0.05, drho=0.0)
+    u[0] += 0.08  # mean flow
+    sim = Simulation(24, 24, 24, precision="f32", collision="srt", tau=0.55)
+    sim.init(rho.cuda(), u.cuda())
+    j0 = np.array(sim.reduce()["momentum"])
+    sim.step(1000)
+    j1 = np.array(sim.reduce()["momentum"])
+    drift = float(np.abs(j1 - j0).max() / np.abs(j0).max())
+    print("FP32 global momentum drift over 1000 steps: %.2e" % drift)
+    assert drift < 1e-6
