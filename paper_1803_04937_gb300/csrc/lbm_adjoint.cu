@@ -134,11 +134,11 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
                                                       AdjConst<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
-    __shared__ double sh[32];
+    __shared__ float shp[256], shm[256];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    double gp_acc = 0.0, gm_acc = 0.0;
+    float gp_cell = 0.0f, gm_cell = 0.0f;  // this cell's terms of dL/domega+ and dL/domega-
     if (x < g.nx && y < g.ny) {
         Cell c(x, y, z, g);
         const int self = c.self();
@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
         adj_pair<R, 6>(e, mu, p.fraw, cgp, cgm, cf_);
         adj_pair<R, 7>(e, mu, p.fraw, cgp, cgm, cf_);
         adj_pair<R, 8>(e, mu, p.fraw, cgp, cgm, cf_);
-        gp_acc = -((double)(mu[0] * (f[0] - e.eq0)) + 0.5 * (double)cgp);
-        gm_acc = -0.5 * (double)cgm - 0.5 * (double)cf_;
+        gp_cell = (float)(-(mu[0] * (f[0] - e.eq0) + R(0.5) * cgp));
+        gm_cell = (float)(R(-0.5) * (cgm + cf_));
         // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
         R Ssum_f = R(0), Ssum_e = R(0);
         R face[3] = {R(0), R(0), R(0)}, edge[3] = {R(0), R(0), R(0)};
@@ -223,28 +223,30 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] + t + hd - cg);
         }
     }
+    // Block partial in FP64: the per-cell terms are staged in shared memory
+    // and one warp accumulates them in double (fixed order), which keeps the
+    // FP64 instruction count per cell low on this GPU's FP64 pipe.
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    double s0 = gp_acc, s1 = gm_acc;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o);
-        s1 += __shfl_down_sync(0xffffffffu, s1, o);
-    }
-    const int lane = tid & 31, warp = tid >> 5, nwarp = (blockDim.x * blockDim.y) >> 5;
-    if (lane == 0) {
-        sh[warp] = s0;
-        sh[16 + warp] = s1;
-    }
+    const int nthreads = blockDim.x * blockDim.y;
+    shp[tid] = gp_cell;
+    shm[tid] = gm_cell;
     __syncthreads();
-    if (tid == 0) {
+    if (tid < 32) {
         double a0 = 0.0, a1 = 0.0;
-        for (int w = 0; w < nwarp; ++w) {
-            a0 += sh[w];
-            a1 += sh[16 + w];
+        for (int i = tid; i < nthreads; i += 32) {
+            a0 += (double)shp[i];
+            a1 += (double)shm[i];
         }
-        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partial[2 * b] = a0;
-        partial[2 * b + 1] = a1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        }
+        if (tid == 0) {
+            const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            partial[2 * b] = a0;
+            partial[2 * b + 1] = a1;
+        }
     }
 }
 

@@ -295,7 +295,7 @@ __device__ __forceinline__ void gather2(const Planes<T> &P, const Site<WALLS> &s
 }
 
 template <typename T, bool RHO0, bool WALLS>
-__global__ void __launch_bounds__(256) k_ab2(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
+__global__ void __launch_bounds__(256, 4) k_ab2(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     const int lane = threadIdx.x & 31;
