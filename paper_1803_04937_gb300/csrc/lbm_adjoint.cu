@@ -134,11 +134,11 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
                                                       AdjConst<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
-    __shared__ float shp[256], shm[256];
+    __shared__ typename Storage<T>::R shp[256], shm[256];  // compute precision
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    float gp_cell = 0.0f, gm_cell = 0.0f;  // this cell's terms of dL/domega+ and dL/domega-
+    R gp_cell = R(0), gm_cell = R(0);  // this cell's terms of dL/domega+ and dL/domega-
     if (x < g.nx && y < g.ny) {
         Cell c(x, y, z, g);
         const int self = c.self();
@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
         adj_pair<R, 6>(e, mu, p.fraw, cgp, cgm, cf_);
         adj_pair<R, 7>(e, mu, p.fraw, cgp, cgm, cf_);
         adj_pair<R, 8>(e, mu, p.fraw, cgp, cgm, cf_);
-        gp_cell = (float)(-(mu[0] * (f[0] - e.eq0) + R(0.5) * cgp));
-        gm_cell = (float)(R(-0.5) * (cgm + cf_));
+        gp_cell = -(mu[0] * (f[0] - e.eq0) + R(0.5) * cgp);
+        gm_cell = R(-0.5) * (cgm + cf_);
         // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
         R Ssum_f = R(0), Ssum_e = R(0);
         R face[3] = {R(0), R(0), R(0)}, edge[3] = {R(0), R(0), R(0)};
@@ -223,9 +223,10 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] + t + hd - cg);
         }
     }
-    // Block partial in FP64: the per-cell terms are staged in shared memory
-    // and one warp accumulates them in double (fixed order), which keeps the
-    // FP64 instruction count per cell low on this GPU's FP64 pipe.
+    // Block partial in FP64: the per-cell terms are staged in shared memory (in
+    // the compute precision) and one warp accumulates them in double (fixed
+    // order), which keeps the FP64 instruction count per cell low on this GPU's
+    // FP64 pipe.
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
     shp[tid] = gp_cell;

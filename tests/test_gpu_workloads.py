@@ -60,11 +60,14 @@ def _shear_amp_phase(uy, n):
     return abs(c), np.angle(c)
 
 
-# FP32 storage rounds every population to 24 bits each step; in slow flows the
-# rounding errors of a slowly varying field are correlated from step to step, so
-# after thousands of steps the velocity error against the FP64 oracle grows to
-# ~1e-5..1e-4 of max|u| (measured and printed below).  The tests assert 2e-4.
-FP32_LONG_TOL = 2e-4
+# FP32 runs against the FP64 oracle: the equilibrium's first moment is exact in
+# FP32 (lbm_device.cuh), so the remaining error is rounding.  The velocity used
+# in the equilibrium is the rounded sum of the stored populations, and the
+# antisymmetric relaxation feeds its rounding error back into the momentum each
+# step (factor omega-); in slowly varying flows these errors are partly
+# coherent, giving ~1e-6 ... 2e-5 of max|u| after thousands of steps (measured
+# and printed below).  The long runs assert 2e-5.
+FP32_LONG_TOL = 2e-5
 
 
 @pytest.mark.parametrize("collision", ["srt", "trt"])
