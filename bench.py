@@ -48,7 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--equilibrium", choices=["standard", "improved"], default="improved")
     p.add_argument("--tau", type=float, default=0.8)
     p.add_argument("--block", type=str, default=None, help="step kernel block 'bx,by'")
-    p.add_argument("--cells-x", type=int, choices=[1, 2], default=None,
+    p.add_argument("--cells-x", type=int, choices=[1, 2, 4], default=None,
                    help="step kernel cells per thread along x (default: library's choice)")
     p.add_argument("--only-adjoint", action="store_true",
                    help="time only the adjoint workload (128^3) and print its figures")

@@ -93,9 +93,10 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_OPT_COLLISION 12  /* LBM_SRT or LBM_TRT */
 #define LBM_OPT_BLOCK_X   13  /* step kernel threads per block along x (tuning) */
 #define LBM_OPT_BLOCK_Y   14  /* ... along y; bx * by <= 256 and a multiple of 32 */
-#define LBM_OPT_CELLS_X   15  /* cells per thread along x in the step kernel: 1, or 2
-                                 (paired accesses; used when nx is even and bx is a multiple
-                                 of 32).  Default 2 for 16-bit storage, 1 otherwise. */
+#define LBM_OPT_CELLS_X   15  /* cells per thread along x in the step kernel: 1; 2 (paired
+                                 accesses; nx even, bx a multiple of 32); or 4 (16-bit storage,
+                                 A/B pattern, nx a multiple of 4, bx * by <= 128; otherwise
+                                 treated as 2).  Default 2 for 16-bit storage, 1 otherwise. */
 
 /* lbm_reduce output slots */
 #define LBM_RED_MASS      0   /* sum_x rho */

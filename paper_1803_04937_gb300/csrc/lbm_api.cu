@@ -244,7 +244,7 @@ int lbm_set_option(lbm_handle h, int key, double v)
         h->collision = (int)v;
         return LBM_OK;
     case LBM_OPT_CELLS_X:
-        if (v != 1.0 && v != 2.0) return fail(h, LBM_EINVAL, "cells per thread must be 1 or 2");
+        if (v != 1.0 && v != 2.0 && v != 4.0) return fail(h, LBM_EINVAL, "cells per thread must be 1, 2 or 4");
         h->cells_x = (int)v;
         return LBM_OK;
     case LBM_OPT_BLOCK_X:

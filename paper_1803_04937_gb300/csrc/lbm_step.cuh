@@ -253,23 +253,43 @@ __device__ __forceinline__ void gather2(const Planes<T> &P, const Site<WALLS> &s
     const bool last = lane == 31 || x0 + 2 >= g.nx;
     // Phase 1: issue every load before any shuffle.  lo/hi: the own pair of
     // the source row (or, through a y/z wall, the own cell's reflected pair);
-    // e: the element beyond the segment's edge for the +-x populations.
+    // e: the element beyond the segment's edge for the +-x populations.  In a
+    // warp away from the row ends (warp-uniform test) that element sits right
+    // next to the pair, one element before or two after it, so its address is
+    // the pair's address plus a constant; the first and last warp of a row
+    // take the general path with the periodic wrap and the x walls.
     R lo[Q], hi[Q], e[Q];
+    const bool row_end = __any_sync(0xffffffffu, x0 == 0 || x0 + 2 >= g.nx);
+    if (!row_end) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int cx = CX(q);
-        const bool w = s.template wall_yz<-1>(q);
-        const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
-        const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
-        const int srow = s.template row_along<-1>(q);
-        Pair<T>::load(w ? bnc + s.own + x0 : src + srow + x0, lo[q], hi[q]);
-        e[q] = R(0);
-        if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
-            const T *a = (WALLS && s.bxm) ? bnc + s.own + x0 : src + srow + s.xm;
-            if (lane == 0 && active && !w) e[q] = Storage<T>::load(a);
-        } else if (cx < 0) {  // pull from x + 1: the segment's last lane needs element x0 + 2
-            const T *a = (WALLS && s.bxp) ? bnc + s.own + x0 + 1 : src + srow + s.xp;
-            if (last && active && !w) e[q] = Storage<T>::load(a);
+        for (int q = 0; q < Q; ++q) {
+            const int cx = CX(q);
+            const bool w = s.template wall_yz<-1>(q);
+            const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
+            const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
+            const T *ps = src + s.template row_along<-1>(q) + x0;
+            Pair<T>::load(w ? bnc + s.own + x0 : ps, lo[q], hi[q]);
+            e[q] = R(0);
+            if (cx > 0 && lane == 0 && !w) e[q] = Storage<T>::load(ps - 1);
+            if (cx < 0 && lane == 31 && !w) e[q] = Storage<T>::load(ps + 2);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int cx = CX(q);
+            const bool w = s.template wall_yz<-1>(q);
+            const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
+            const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
+            const int srow = s.template row_along<-1>(q);
+            Pair<T>::load(w ? bnc + s.own + x0 : src + srow + x0, lo[q], hi[q]);
+            e[q] = R(0);
+            if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
+                const T *a = (WALLS && s.bxm) ? bnc + s.own + x0 : src + srow + s.xm;
+                if (lane == 0 && active && !w) e[q] = Storage<T>::load(a);
+            } else if (cx < 0) {  // pull from x + 1: the segment's last lane needs element x0 + 2
+                const T *a = (WALLS && s.bxp) ? bnc + s.own + x0 + 1 : src + srow + s.xp;
+                if (last && active && !w) e[q] = Storage<T>::load(a);
+            }
         }
     }
     // Phase 2: assemble the shifted pairs.
@@ -398,6 +418,132 @@ __global__ void __launch_bounds__(256, 2) k_aa_odd2(Planes<T> P, Geo g, Relax<ty
     }
 }
 
+// ---------------------------------------------------------------- four cells per thread (16-bit storage)
+
+// Raw 16-bit codes <-> float for the 16-bit storage types.
+template <typename T> struct Bits16;
+template <> struct Bits16<__half> {
+    static __device__ __forceinline__ float to_float(unsigned int b)
+    {
+        return __half2float(__ushort_as_half((unsigned short)b));
+    }
+    static __device__ __forceinline__ unsigned int from_float(float v)
+    {
+        return __half_as_ushort(__float2half_rn(v));
+    }
+};
+template <> struct Bits16<__nv_bfloat16> {
+    static __device__ __forceinline__ float to_float(unsigned int b)
+    {
+        return __bfloat162float(__ushort_as_bfloat16((unsigned short)b));
+    }
+    static __device__ __forceinline__ unsigned int from_float(float v)
+    {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+};
+
+// Element c (0..3) of four 16-bit codes packed in a uint2, and its replacement.
+template <int c>
+__device__ __forceinline__ unsigned int quad_get(const uint2 &v)
+{
+    const unsigned int w = c < 2 ? v.x : v.y;
+    return (c & 1) ? (w >> 16) : (w & 0xffffu);
+}
+template <int c>
+__device__ __forceinline__ void quad_set(uint2 &v, unsigned int b)
+{
+    unsigned int &w = c < 2 ? v.x : v.y;
+    w = (c & 1) ? ((w & 0x0000ffffu) | (b << 16)) : ((w & 0xffff0000u) | (b & 0xffffu));
+}
+
+// A/B pull step for 16-bit storage, four cells (x0 .. x0 + 3) per thread,
+// x0 a multiple of 4, nx a multiple of 4: every population is read and
+// written as one 8-byte quad, so the address work and the edge handling are
+// shared by four cells.  The quads are kept as raw 16-bit codes; the four
+// cells are collided one after another and their results written back into
+// the quads in place (ascending order: a +x population of cell c reads the
+// element c - 1, whose input is kept in `carry` before cell c - 1 overwrites
+// it).  Bitwise the same results as the one- and two-cell kernels.
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Geo g, Relax<float> p)
+{
+    const int lane = threadIdx.x & 31;
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    const Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
+    const int xs = s.x;
+    const bool last = lane == 31 || xs + 4 >= g.nx;
+    const bool row_end = __any_sync(0xffffffffu, xs == 0 || xs + 4 >= g.nx);
+    // Phase 1: loads.  e: the element beyond the segment's edge (x0 - 1 for
+    // +x populations, x0 + 4 for -x populations), loaded by the edge lane.
+    uint2 quad[Q];
+    unsigned int e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const bool w = s.template wall_yz<-1>(q);
+        const unsigned short *srcq = reinterpret_cast<const unsigned short *>(src.p[q]);
+        const unsigned short *bncq = reinterpret_cast<const unsigned short *>(src.p[OPP(q)]);
+        const int srow = s.template row_along<-1>(q);
+        const unsigned short *ps = srcq + srow + xs;
+        quad[q] = *reinterpret_cast<const uint2 *>(w ? bncq + s.own + xs : ps);
+        e[q] = 0u;
+        if (cx > 0) {
+            const unsigned short *a = row_end ? ((WALLS && s.bxm) ? bncq + s.own + xs : srcq + srow + s.xm) : ps - 1;
+            if (lane == 0 && active && !w) e[q] = *a;
+        } else if (cx < 0) {
+            const unsigned short *a = row_end ? ((WALLS && s.bxp) ? bncq + s.own + xs + 3 : srcq + srow + s.xp) : ps + 4;
+            if (last && active && !w) e[q] = *a;
+        }
+    }
+    // Phase 2: neighbour elements across the lanes.
+    unsigned int carry[Q], right[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        carry[q] = 0u;
+        right[q] = 0u;
+        if (cx > 0) {
+            unsigned int l = __shfl_up_sync(0xffffffffu, quad[q].y >> 16, 1);
+            carry[q] = lane == 0 ? e[q] : l;
+        } else if (cx < 0) {
+            unsigned int r = __shfl_down_sync(0xffffffffu, quad[q].x & 0xffffu, 1);
+            right[q] = last ? e[q] : r;
+        }
+    }
+    if (!active) return;
+    // Phase 3: four collisions, results written into the quads in place.
+#define LBM_AB4_CELL(c)                                                                      \
+    {                                                                                        \
+        float f[Q];                                                                          \
+        _Pragma("unroll") for (int q = 0; q < Q; ++q)                                        \
+        {                                                                                    \
+            const int cx = CX(q);                                                            \
+            const bool w = s.template wall_yz<-1>(q);                                        \
+            unsigned int b;                                                                  \
+            if (cx == 0 || w) b = quad_get<c>(quad[q]);                                      \
+            else if (cx > 0) b = carry[q];                                                   \
+            else b = (c == 3) ? right[q] : quad_get<(c + 1) & 3>(quad[q]);                   \
+            f[q] = Bits16<T>::to_float(b);                                                   \
+        }                                                                                    \
+        collide_lean<float, RHO0>(f, p);                                                     \
+        _Pragma("unroll") for (int q = 0; q < Q; ++q)                                        \
+        {                                                                                    \
+            if (CX(q) > 0) carry[q] = quad_get<c>(quad[q]);                                   \
+            quad_set<c>(quad[q], Bits16<T>::from_float(f[q]));                                \
+        }                                                                                    \
+    }
+    LBM_AB4_CELL(0) LBM_AB4_CELL(1) LBM_AB4_CELL(2) LBM_AB4_CELL(3)
+#undef LBM_AB4_CELL
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(dst.p[q]) + s.own + xs) = quad[q];
+}
+
 // ---------------------------------------------------------------- dispatch
 
 template <typename T, bool RHO0, bool WALLS>
@@ -407,12 +553,20 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
     using R = typename Storage<T>::R;
     const Relax<R> p = to_relax<R>(cb);
     const dim3 block(ls.bx, ls.by, 1);
-    const bool pairs = ls.cells_x == 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
-    const int span = pairs ? 2 * ls.bx : ls.bx;
+    const bool quads = sizeof(T) == 2 && kind == 0 && ls.cells_x == 4 && (g.nx % 4) == 0 && (ls.bx % 32) == 0 &&
+                       ls.bx * ls.by <= 128;
+    const bool pairs = !quads && ls.cells_x >= 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
+    const int span = quads ? 4 * ls.bx : (pairs ? 2 * ls.bx : ls.bx);
     const dim3 grid((g.nx + span - 1) / span, (g.ny + ls.by - 1) / ls.by, g.nz);
     const Planes<T> D = planes_of<T>(dst, g.ncell);
     if (kind == 0) {
         const Planes<T> S = planes_of<T>(src, g.ncell);
+        if constexpr (sizeof(T) == 2) {
+            if (quads) {
+                k_ab4<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
+                return cudaGetLastError();
+            }
+        }
         if (pairs)
             k_ab2<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
         else

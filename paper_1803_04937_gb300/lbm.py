@@ -74,6 +74,7 @@ class Simulation:
         self._set(_lib.OPT_RHO0_MODE, 1.0 if rho0_is_rho else 0.0)
         self._set(_lib.OPT_PATTERN, _PATTERN[pattern])
         if block is not None:
+            self._set(_lib.OPT_BLOCK_Y, 1)  # keep bx * by valid while changing bx
             self._set(_lib.OPT_BLOCK_X, block[0])
             self._set(_lib.OPT_BLOCK_Y, block[1])
         if cells_x is not None:

@@ -65,11 +65,12 @@ def test_step_matches_oracle(case, mapping, pattern, precision):
 
 @pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s", "f64"])
 @pytest.mark.parametrize("case", [0, 3, 5])
-@pytest.mark.parametrize("nx", [45, 130])
+@pytest.mark.parametrize("nx", [45, 130, 388])
 def test_aa_equals_ab_bitwise(nx, case, precision):
-    """AA and A/B, with one or two cells per thread, run the same arithmetic per
-    cell: identical bits after any number of steps (also a race check of the
-    in-place pattern)."""
+    """AA and A/B, with one, two or four cells per thread, run the same
+    arithmetic per cell: identical bits after any number of steps (also a race
+    check of the in-place pattern).  nx = 388 gives the four-cell 16-bit kernel
+    interior warps as well as the row-end warps."""
     kw = CASES[case]
     shape = (6, 11, nx)
     rho, u = random_fields(shape, seed=7)
@@ -77,7 +78,9 @@ def test_aa_equals_ab_bitwise(nx, case, precision):
         sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=1)
         sb, _, _ = _run_gpu(shape, rho, u, steps, precision, "aa", kw, cells_x=2)
         sc, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=2)
+        sd, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=4)
         assert torch.equal(sa.get_pdfs(), sc.get_pdfs())
+        assert torch.equal(sa.get_pdfs(), sd.get_pdfs())
         assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
         ra, ua = sa.moments(torch.float32)
         rb, ub = sb.moments(torch.float32)
