@@ -187,8 +187,9 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
         h->bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
         h->by = 256 / h->bx;
     }
-    // 16-bit storage needs paired accesses to reach the bandwidth roofline
-    h->cells_x = (precision == LBM_F16S || precision == LBM_BF16S) ? 2 : 1;
+    // 16-bit storage needs wide accesses shared by several cells to approach
+    // the bandwidth roofline: four cells per thread (A/B; the AA steps use two)
+    h->cells_x = (precision == LBM_F16S || precision == LBM_BF16S) ? 4 : 1;
     *out = h;
     return LBM_OK;
 }

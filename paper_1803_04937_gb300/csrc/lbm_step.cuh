@@ -253,43 +253,23 @@ __device__ __forceinline__ void gather2(const Planes<T> &P, const Site<WALLS> &s
     const bool last = lane == 31 || x0 + 2 >= g.nx;
     // Phase 1: issue every load before any shuffle.  lo/hi: the own pair of
     // the source row (or, through a y/z wall, the own cell's reflected pair);
-    // e: the element beyond the segment's edge for the +-x populations.  In a
-    // warp away from the row ends (warp-uniform test) that element sits right
-    // next to the pair, one element before or two after it, so its address is
-    // the pair's address plus a constant; the first and last warp of a row
-    // take the general path with the periodic wrap and the x walls.
+    // e: the element beyond the segment's edge for the +-x populations.
     R lo[Q], hi[Q], e[Q];
-    const bool row_end = __any_sync(0xffffffffu, x0 == 0 || x0 + 2 >= g.nx);
-    if (!row_end) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int cx = CX(q);
-            const bool w = s.template wall_yz<-1>(q);
-            const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
-            const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
-            const T *ps = src + s.template row_along<-1>(q) + x0;
-            Pair<T>::load(w ? bnc + s.own + x0 : ps, lo[q], hi[q]);
-            e[q] = R(0);
-            if (cx > 0 && lane == 0 && !w) e[q] = Storage<T>::load(ps - 1);
-            if (cx < 0 && lane == 31 && !w) e[q] = Storage<T>::load(ps + 2);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int cx = CX(q);
-            const bool w = s.template wall_yz<-1>(q);
-            const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
-            const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
-            const int srow = s.template row_along<-1>(q);
-            Pair<T>::load(w ? bnc + s.own + x0 : src + srow + x0, lo[q], hi[q]);
-            e[q] = R(0);
-            if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
-                const T *a = (WALLS && s.bxm) ? bnc + s.own + x0 : src + srow + s.xm;
-                if (lane == 0 && active && !w) e[q] = Storage<T>::load(a);
-            } else if (cx < 0) {  // pull from x + 1: the segment's last lane needs element x0 + 2
-                const T *a = (WALLS && s.bxp) ? bnc + s.own + x0 + 1 : src + srow + s.xp;
-                if (last && active && !w) e[q] = Storage<T>::load(a);
-            }
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const bool w = s.template wall_yz<-1>(q);
+        const T *src = SWAP ? P.p[OPP(q)] : P.p[q];
+        const T *bnc = SWAP ? P.p[q] : P.p[OPP(q)];
+        const int srow = s.template row_along<-1>(q);
+        Pair<T>::load(w ? bnc + s.own + x0 : src + srow + x0, lo[q], hi[q]);
+        e[q] = R(0);
+        if (cx > 0) {  // pull from x - 1: lane 0 needs element x0 - 1
+            const T *a = (WALLS && s.bxm) ? bnc + s.own + x0 : src + srow + s.xm;
+            if (lane == 0 && active && !w) e[q] = Storage<T>::load(a);
+        } else if (cx < 0) {  // pull from x + 1: the segment's last lane needs element x0 + 2
+            const T *a = (WALLS && s.bxp) ? bnc + s.own + x0 + 1 : src + srow + s.xp;
+            if (last && active && !w) e[q] = Storage<T>::load(a);
         }
     }
     // Phase 2: assemble the shifted pairs.
@@ -553,20 +533,25 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
     using R = typename Storage<T>::R;
     const Relax<R> p = to_relax<R>(cb);
     const dim3 block(ls.bx, ls.by, 1);
-    const bool quads = sizeof(T) == 2 && kind == 0 && ls.cells_x == 4 && (g.nx % 4) == 0 && (ls.bx % 32) == 0 &&
-                       ls.bx * ls.by <= 128;
+    const bool quads = sizeof(T) == 2 && kind == 0 && ls.cells_x == 4 && (g.nx % 4) == 0;
     const bool pairs = !quads && ls.cells_x >= 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
-    const int span = quads ? 4 * ls.bx : (pairs ? 2 * ls.bx : ls.bx);
+    if (quads) {
+        // 128 threads; as many along x as one row needs (a multiple of 32), the rest along y
+        const int bx = min(128, max(32, ((g.nx / 4 + 31) / 32) * 32));
+        const dim3 block4(bx, 128 / bx, 1);
+        const dim3 grid4((g.nx + 4 * bx - 1) / (4 * bx), (g.ny + block4.y - 1) / block4.y, g.nz);
+        if constexpr (sizeof(T) == 2) {
+            const Planes<T> S = planes_of<T>(src, g.ncell);
+            const Planes<T> D = planes_of<T>(dst, g.ncell);
+            k_ab4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(S, D, g, p);
+        }
+        return cudaGetLastError();
+    }
+    const int span = pairs ? 2 * ls.bx : ls.bx;
     const dim3 grid((g.nx + span - 1) / span, (g.ny + ls.by - 1) / ls.by, g.nz);
     const Planes<T> D = planes_of<T>(dst, g.ncell);
     if (kind == 0) {
         const Planes<T> S = planes_of<T>(src, g.ncell);
-        if constexpr (sizeof(T) == 2) {
-            if (quads) {
-                k_ab4<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
-                return cudaGetLastError();
-            }
-        }
         if (pairs)
             k_ab2<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
         else
