@@ -261,3 +261,26 @@ def test_duct_convergence_orders():
     orders = [math.log2(r[i] / r[i + 1]) for i in range(2)]
     print("duct Lambda^2=4/25 S ratios %s, observed orders %s" % (r, orders))
     assert 1.6 < orders[-1] < 2.4
+
+
+def test_shear_wave_with_normal_background_flow():
+    """Shear wave u_y(x) with a background flow U_z normal to the wave plane:
+    D3Q19-I evolves (u_x, u_y) exactly as without U_z (its projection onto
+    (c_x, c_y) is D2Q9 for any u_z; Eq. 22), D3Q19-S does not."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    n, steps = 128, 500
+    out = {}
+    for equilibrium in ("standard", "improved"):
+        res = []
+        for Uz in (0.0, 0.1):
+            rho, u = inputs.shear_wave(n, 4, 4, U=(0.05, 0.0, Uz), amplitude=0.01, device="cuda")
+            sim = Simulation(n, 4, 4, precision="f64", equilibrium=equilibrium, collision="srt", tau=0.6)
+            sim.init(rho, u)
+            sim.step(steps)
+            _, ug = sim.moments()
+            res.append(ug[:2].cpu().numpy())
+        out[equilibrium] = float(np.abs(res[1] - res[0]).max() / np.abs(res[0]).max())
+    print("shear wave with U_z = 0.1 vs U_z = 0: max rel change of (u_x, u_y)  S = %.3e   I = %.3e"
+          % (out["standard"], out["improved"]))
+    assert out["improved"] < 1e-13
+    assert out["standard"] > 1e-6
