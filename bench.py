@@ -406,7 +406,7 @@ def run_native(args):
     per_launch = t_local / args.steps
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LUP[args.precision] * cells / per_launch / 1e9
-    cx = args.cells_x or (2 if args.precision in ("f16s", "bf16s") else 1)
+    cx = args.cells_x or (4 if args.precision in ("f16s", "bf16s") else 1)
     if args.pattern == "ab":
         kname = "k_ab%d<%s>" % (cx, args.precision)
     else:

@@ -15,8 +15,8 @@ Contents
   exact rational arithmetic.
 
 Arrays: macroscopic fields are numpy arrays ``rho[nz, ny, nx]`` and
-``u[3, nz, ny, nx]``; populations are ``f[nz, ny, nx, 19]`` in the oracle's
-own direction order (see ``velocity_set``).
+``u[3, nz, ny, nx]``; populations are ``f[nz, ny, nx, Q]`` (Q = 19, or 27 for
+the D3Q27 lattice) in the oracle's own direction order (see ``velocity_set``).
 """
 import ctypes
 import dataclasses
@@ -39,6 +39,7 @@ class _Cfg(ctypes.Structure):
         ("nthreads", ctypes.c_int),
         ("tau", ctypes.c_double), ("trt_magic", ctypes.c_double),
         ("accel", ctypes.c_double * 3),
+        ("stencil", ctypes.c_int),
     ]
 
 
@@ -51,7 +52,11 @@ def _load():
         ip = ctypes.POINTER(ctypes.c_int)
         cp = ctypes.POINTER(_Cfg)
         lib.oracle_velocity_set.argtypes = [ip, dp, ip]
+        lib.oracle_velocity_set_of.argtypes = [ctypes.c_int, ip, dp, ip]
+        lib.oracle_velocity_set_of.restype = ctypes.c_int
         lib.oracle_equilibrium_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, dp, dp, dp]
+        lib.oracle_equilibrium_field_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long, dp, dp,
+                                                    dp]
         lib.oracle_init.argtypes = [cp, dp, dp, dp]
         lib.oracle_step.argtypes = [cp, dp, dp]
         lib.oracle_moments.argtypes = [cp, dp, dp, dp]
@@ -95,10 +100,15 @@ class Config:
     walls: tuple = (False, False, False)  # half-way bounce-back on both ends of an axis
     rho0_is_rho: bool = False        # rho0 = 1 (paper's choice) or rho0 = rho
     nthreads: int = 0                # OpenMP threads for oracle_step (0: default)
+    stencil: int = 19                # 19 (D3Q19) or 27 (D3Q27, standard equilibrium)
 
     @property
     def shape(self):
         return (self.nz, self.ny, self.nx)
+
+    @property
+    def Q(self):
+        return 27 if self.stencil == 27 else 19
 
     @property
     def ncell(self):
@@ -116,30 +126,36 @@ class Config:
         c.nthreads = int(self.nthreads)
         c.tau = float(self.tau)
         c.trt_magic = float(self.trt_magic)
+        c.stencil = int(self.stencil)
         return c
 
 
-def velocity_set():
-    """D3Q19 velocities c[19,3], weights w[19] and opposite index opp[19] (Sec. 2.3)."""
+def velocity_set(stencil=19):
+    """Velocities c[Q,3], weights w[Q] and opposite index opp[Q] of D3Q19 (default)
+    or D3Q27 (Sec. 2.3), in the oracle's own order."""
     lib = _load()
-    c = np.zeros((Q, 3), dtype=np.int32)
-    w = np.zeros(Q)
-    opp = np.zeros(Q, dtype=np.int32)
-    lib.oracle_velocity_set(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
-                            opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    nq = 27 if stencil == 27 else 19
+    c = np.zeros((nq, 3), dtype=np.int32)
+    w = np.zeros(nq)
+    opp = np.zeros(nq, dtype=np.int32)
+    lib.oracle_velocity_set_of(int(stencil), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
+                               opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     return c, w, opp
 
 
-def equilibrium(kind, rho, u, rho0_is_rho=False):
-    """feq[..., 19] for rho[...] and u[3, ...]: Eq. 14 (second order) or Eq. 22."""
+def equilibrium(kind, rho, u, rho0_is_rho=False, stencil=19):
+    """feq[..., Q] for rho[...] and u[3, ...]: Eq. 14 (second order) or, on
+    D3Q19, Eq. 22."""
     lib = _load()
+    nq = 27 if stencil == 27 else 19
     rho = _f64(rho)
     shape = rho.shape
     n = rho.size
     u = _f64(np.asarray(u).reshape(3, n))
-    feq = np.zeros((n, Q))
-    lib.oracle_equilibrium_field(int(kind), int(bool(rho0_is_rho)), n, _dp(rho.reshape(n)), _dp(u), _dp(feq))
-    return feq.reshape(shape + (Q,))
+    feq = np.zeros((n, nq))
+    lib.oracle_equilibrium_field_of(int(stencil), int(kind), int(bool(rho0_is_rho)), n, _dp(rho.reshape(n)), _dp(u),
+                                    _dp(feq))
+    return feq.reshape(shape + (nq,))
 
 
 def init(cfg: Config, rho, u):
@@ -147,7 +163,7 @@ def init(cfg: Config, rho, u):
     lib = _load()
     rho = _f64(rho).reshape(cfg.shape)
     u = _f64(u).reshape((3,) + cfg.shape)
-    f = np.zeros(cfg.shape + (Q,))
+    f = np.zeros(cfg.shape + (cfg.Q,))
     c = cfg._c()
     lib.oracle_init(ctypes.byref(c), _dp(rho), _dp(u), _dp(f))
     return f
@@ -156,7 +172,7 @@ def init(cfg: Config, rho, u):
 def step(cfg: Config, f, nsteps=1):
     """nsteps updates of Eq. 15 (collide, then push-stream)."""
     lib = _load()
-    a = _f64(f).reshape(cfg.shape + (Q,)).copy()
+    a = _f64(f).reshape(cfg.shape + (cfg.Q,)).copy()
     b = np.empty_like(a)
     c = cfg._c()
     for _ in range(nsteps):
@@ -168,7 +184,7 @@ def step(cfg: Config, f, nsteps=1):
 def moments(cfg: Config, f):
     """rho (Eq. 16) and u (Eq. 17) of the populations f."""
     lib = _load()
-    f = _f64(f).reshape(cfg.shape + (Q,))
+    f = _f64(f).reshape(cfg.shape + (cfg.Q,))
     rho = np.zeros(cfg.shape)
     u = np.zeros((3,) + cfg.shape)
     c = cfg._c()
@@ -198,7 +214,7 @@ def max_threads():
 def loss_velocity_l2(cfg: Config, f, u_target):
     """L = 1/2 sum_x |u(x) - u_target(x)|^2 and dL/df (rho0 = 1)."""
     lib = _load()
-    f = _f64(f).reshape(cfg.shape + (Q,))
+    f = _f64(f).reshape(cfg.shape + (cfg.Q,))
     tgt = _f64(u_target).reshape((3,) + cfg.shape)
     lam = np.zeros_like(f)
     L = ctypes.c_double(0.0)
@@ -211,8 +227,8 @@ def loss_velocity_l2(cfg: Config, f, u_target):
 def adjoint_step(cfg: Config, f_t, lam_next):
     """(lam_t, [dL/domega+, dL/domega-] contribution) for one step from state f_t."""
     lib = _load()
-    f_t = _f64(f_t).reshape(cfg.shape + (Q,))
-    lam_next = _f64(lam_next).reshape(cfg.shape + (Q,))
+    f_t = _f64(f_t).reshape(cfg.shape + (cfg.Q,))
+    lam_next = _f64(lam_next).reshape(cfg.shape + (cfg.Q,))
     lam = np.zeros_like(f_t)
     g = np.zeros(2)
     c = cfg._c()
@@ -225,7 +241,7 @@ def adjoint_init_velocity(cfg: Config, u0, lam0):
     """dL/du0 from lam0 = dL/df(t=0), through f(0) = feq(rho, u0)."""
     lib = _load()
     u0 = _f64(u0).reshape((3,) + cfg.shape)
-    lam0 = _f64(lam0).reshape(cfg.shape + (Q,))
+    lam0 = _f64(lam0).reshape(cfg.shape + (cfg.Q,))
     g = np.zeros((3,) + cfg.shape)
     c = cfg._c()
     if lib.oracle_adjoint_init_velocity(ctypes.byref(c), _dp(u0), _dp(lam0), _dp(g)) != 0:

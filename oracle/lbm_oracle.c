@@ -9,11 +9,13 @@
  * library itself.  It shares no code, tables or headers with the CUDA path.
  *
  * Conventions (all lattice units, dx = dt = 1, c_s^2 = 1/3):
- *   - velocity set: D3Q19 of Sec. 2.3 (rest, 6 faces, 12 edges), built here by
- *     enumerating {-1,0,1}^3 and keeping |c|^2 <= 2, in this file's own order;
- *     weights 1/3, 1/18, 1/36 (Sec. 2.3).
- *   - state: f[((z*ny + y)*nx + x)*19 + q], the post-streaming, pre-collision
- *     populations f_q(x, t) of Eq. 15.
+ *   - velocity sets (Sec. 2.3), built here by enumerating {-1,0,1}^3 in this
+ *     file's own order: D3Q19 keeps |c|^2 <= 2 (rest, 6 faces, 12 edges;
+ *     weights 1/3, 1/18, 1/36); D3Q27 keeps all 27 (weights 8/27, 2/27, 1/54,
+ *     1/216).  On D3Q27 the moment-matching construction gives the standard
+ *     equilibrium (Sec. 3.1), so both equilibrium choices are Eq. 14 there.
+ *   - state: f[((z*ny + y)*nx + x)*Q + q] (Q = 19 or 27), the post-streaming,
+ *     pre-collision populations f_q(x, t) of Eq. 15.
  *   - equilibria: standard D3Q19-S = Eq. 14 truncated at second order in u;
  *     improved D3Q19-I = Eq. 22.  rho0 = 1 (Sec. 2.3, used for all of the
  *     paper's analysis) or rho0 = rho (the compressible variant below Eq. 14).
@@ -29,7 +31,7 @@
  *   - streaming is done by PUSH after collision (the GPU library pulls).
  *
  * The adjoint (reverse-mode derivative of one step; not in the paper) is
- * written as the transpose of the explicitly assembled 19x19 Jacobian of the
+ * written as the transpose of the explicitly assembled QxQ Jacobian of the
  * collision, composed with the transpose of the streaming permutation.  It
  * supports rho0 = 1 only.
  */
@@ -42,7 +44,7 @@
 #include <omp.h>
 #endif
 
-#define Q 19
+#define QMAX 27
 
 typedef struct {
     int nx, ny, nz;
@@ -54,54 +56,86 @@ typedef struct {
     double tau;        /* relaxation time, omega = 1/tau */
     double trt_magic;  /* Lambda = (tau+ - 1/2)(tau- - 1/2) */
     double accel[3];   /* body force a */
+    int stencil;       /* 19 (D3Q19, default when 0) or 27 (D3Q27) */
 } oracle_cfg;
 
-static int C[Q][3];
-static double W[Q];
-static int OPP[Q];
+/* A velocity set: Q velocities C, weights W, opposite index OPP. */
+typedef struct {
+    int Q;
+    int C[QMAX][3];
+    double W[QMAX];
+    int OPP[QMAX];
+} lattice;
+
+static lattice D3Q19, D3Q27;
 static int built = 0;
 
-/* D3Q19 velocities and weights (Sec. 2.3). */
-static void build_lattice(void)
+/* D3Q19 and D3Q27 velocities and weights (Sec. 2.3). */
+static void build_one(lattice *L, int maxnorm)
 {
-    if (built) return;
     int q = 0;
     for (int cx = -1; cx <= 1; ++cx)
         for (int cy = -1; cy <= 1; ++cy)
             for (int cz = -1; cz <= 1; ++cz) {
                 int n = cx * cx + cy * cy + cz * cz;
-                if (n > 2) continue;
-                C[q][0] = cx; C[q][1] = cy; C[q][2] = cz;
-                W[q] = (n == 0) ? 1.0 / 3.0 : (n == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+                if (n > maxnorm) continue;
+                L->C[q][0] = cx; L->C[q][1] = cy; L->C[q][2] = cz;
+                if (maxnorm == 2)
+                    L->W[q] = (n == 0) ? 1.0 / 3.0 : (n == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+                else
+                    L->W[q] = (n == 0) ? 8.0 / 27.0 : (n == 1) ? 2.0 / 27.0 : (n == 2) ? 1.0 / 54.0 : 1.0 / 216.0;
                 ++q;
             }
-    for (int a = 0; a < Q; ++a)
-        for (int b = 0; b < Q; ++b)
-            if (C[a][0] == -C[b][0] && C[a][1] == -C[b][1] && C[a][2] == -C[b][2])
-                OPP[a] = b;
+    L->Q = q;
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b)
+            if (L->C[a][0] == -L->C[b][0] && L->C[a][1] == -L->C[b][1] && L->C[a][2] == -L->C[b][2])
+                L->OPP[a] = b;
+}
+
+static void build_lattice(void)
+{
+    if (built) return;
+    build_one(&D3Q19, 2);
+    build_one(&D3Q27, 3);
     built = 1;
+}
+
+static const lattice *lattice_of(int stencil)
+{
+    build_lattice();
+    return stencil == 27 ? &D3Q27 : &D3Q19;
+}
+
+/* Velocities c[3q+i], weights w[q], opposites opp[q] of the stencil (19 or
+ * 27); returns Q. */
+int oracle_velocity_set_of(int stencil, int *c, double *w, int *opp)
+{
+    const lattice *L = lattice_of(stencil);
+    for (int q = 0; q < L->Q; ++q) {
+        for (int i = 0; i < 3; ++i) c[3 * q + i] = L->C[q][i];
+        w[q] = L->W[q];
+        opp[q] = L->OPP[q];
+    }
+    return L->Q;
 }
 
 void oracle_velocity_set(int *c, double *w, int *opp)
 {
-    build_lattice();
-    for (int q = 0; q < Q; ++q) {
-        for (int i = 0; i < 3; ++i) c[3 * q + i] = C[q][i];
-        w[q] = W[q];
-        opp[q] = OPP[q];
-    }
+    oracle_velocity_set_of(19, c, w, opp);
 }
 
-/* Eq. 14 (second-order part) or Eq. 22, for one cell. */
-static void equilibrium(int kind, double rho, double rho0, const double u[3], double feq[Q])
+/* Eq. 14 (second-order part) or Eq. 22 (D3Q19 only), for one cell. */
+static void equilibrium(const lattice *L, int kind, double rho, double rho0, const double u[3], double *feq)
 {
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    for (int q = 0; q < Q; ++q) {
-        double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
-        int n = C[q][0] * C[q][0] + C[q][1] * C[q][1] + C[q][2] * C[q][2];
+    for (int q = 0; q < L->Q; ++q) {
+        const int *c = L->C[q];
+        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        int n = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
         double bracket;
-        if (kind == 0) {
-            /* D3Q19-S: 3 c.u + 9/2 u_a u_b (c_a c_b - delta_ab / 3) */
+        if (kind == 0 || L->Q == 27) {
+            /* standard: 3 c.u + 9/2 u_a u_b (c_a c_b - delta_ab / 3) */
             bracket = 3.0 * cu + 4.5 * cu * cu - 1.5 * uu;
         } else if (n == 0) {
             /* D3Q19-I, rest */
@@ -112,42 +146,51 @@ static void equilibrium(int kind, double rho, double rho0, const double u[3], do
         } else {
             /* D3Q19-I, edges; sum over i of u_i^2 c_qi^2 */
             double s = 0.0;
-            for (int i = 0; i < 3; ++i) s += u[i] * u[i] * C[q][i] * C[q][i];
+            for (int i = 0; i < 3; ++i) s += u[i] * u[i] * c[i] * c[i];
             bracket = 3.0 * cu - 1.5 * s + 4.5 * cu * cu;
         }
-        feq[q] = W[q] * rho + W[q] * rho0 * bracket;
+        feq[q] = L->W[q] * rho + L->W[q] * rho0 * bracket;
     }
 }
 
-/* d feq_q / d u_i at fixed rho, for rho0 = 1 (the derivative of the two
- * closed forms above, written out by hand). */
-static void equilibrium_du(int kind, const double u[3], double d[Q][3])
+/* d feq_q / d u_i at fixed rho, for rho0 = 1 (the derivative of the closed
+ * forms above, written out by hand). */
+static void equilibrium_du(const lattice *L, int kind, const double u[3], double d[][3])
 {
-    for (int q = 0; q < Q; ++q) {
-        double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
-        int n = C[q][0] * C[q][0] + C[q][1] * C[q][1] + C[q][2] * C[q][2];
+    for (int q = 0; q < L->Q; ++q) {
+        const int *c = L->C[q];
+        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        int n = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
         for (int i = 0; i < 3; ++i) {
-            double ci = C[q][i];
+            double ci = c[i];
             double v;
-            if (kind == 0) v = 3.0 * ci + 9.0 * cu * ci - 3.0 * u[i];
+            if (kind == 0 || L->Q == 27) v = 3.0 * ci + 9.0 * cu * ci - 3.0 * u[i];
             else if (n == 0) v = -2.0 * u[i];
             else if (n == 1) v = 3.0 * ci - 6.0 * u[i] + 12.0 * cu * ci;
             else v = 3.0 * ci - 3.0 * u[i] * ci * ci + 9.0 * cu * ci;
-            d[q][i] = W[q] * v;
+            d[q][i] = L->W[q] * v;
         }
+    }
+}
+
+void oracle_equilibrium_field_of(int stencil, int kind, int rho0_is_rho, long n, const double *rho,
+                                 const double *u, double *feq)
+{
+    const lattice *L = lattice_of(stencil);
+    for (long k = 0; k < n; ++k) {
+        double uk[3] = {u[k], u[n + k], u[2 * n + k]};
+        double rho0 = rho0_is_rho ? rho[k] : 1.0;
+        equilibrium(L, kind, rho[k], rho0, uk, feq + k * L->Q);
     }
 }
 
 void oracle_equilibrium_field(int kind, int rho0_is_rho, long n, const double *rho,
                               const double *u, double *feq)
 {
-    build_lattice();
-    for (long k = 0; k < n; ++k) {
-        double uk[3] = {u[k], u[n + k], u[2 * n + k]};
-        double rho0 = rho0_is_rho ? rho[k] : 1.0;
-        equilibrium(kind, rho[k], rho0, uk, feq + k * Q);
-    }
+    oracle_equilibrium_field_of(19, kind, rho0_is_rho, n, rho, u, feq);
 }
+
+static const lattice *cfg_lattice(const oracle_cfg *cfg) { return lattice_of(cfg->stencil); }
 
 static void omegas(const oracle_cfg *cfg, double *wp, double *wm)
 {
@@ -161,12 +204,13 @@ static void omegas(const oracle_cfg *cfg, double *wp, double *wm)
 }
 
 /* Moments of Eq. 16 and Eq. 17 for one cell. */
-static void cell_moments(const oracle_cfg *cfg, const double *f, double *rho, double *rho0, double u[3])
+static void cell_moments(const oracle_cfg *cfg, const lattice *L, const double *f, double *rho, double *rho0,
+                         double u[3])
 {
     double r = 0.0, j[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < Q; ++q) {
+    for (int q = 0; q < L->Q; ++q) {
         r += f[q];
-        for (int i = 0; i < 3; ++i) j[i] += C[q][i] * f[q];
+        for (int i = 0; i < 3; ++i) j[i] += L->C[q][i] * f[q];
     }
     double r0 = cfg->rho0_is_rho ? r : 1.0;
     for (int i = 0; i < 3; ++i) u[i] = (j[i] + 0.5 * cfg->accel[i]) / r0;
@@ -174,16 +218,22 @@ static void cell_moments(const oracle_cfg *cfg, const double *f, double *rho, do
     *rho0 = r0;
 }
 
-/* Post-collision populations of one cell (Eq. 15, or its TRT split). */
-static void collide(const oracle_cfg *cfg, const double *f, double fs[Q])
+static double force_term(const oracle_cfg *cfg, const lattice *L, int q)
 {
-    double rho, rho0, u[3], feq[Q], wp, wm;
-    cell_moments(cfg, f, &rho, &rho0, u);
-    equilibrium(cfg->equilibrium, rho, rho0, u, feq);
+    const int *c = L->C[q];
+    return 3.0 * L->W[q] * (c[0] * cfg->accel[0] + c[1] * cfg->accel[1] + c[2] * cfg->accel[2]);
+}
+
+/* Post-collision populations of one cell (Eq. 15, or its TRT split). */
+static void collide(const oracle_cfg *cfg, const lattice *L, const double *f, double *fs)
+{
+    double rho, rho0, u[3], feq[QMAX], wp, wm;
+    cell_moments(cfg, L, f, &rho, &rho0, u);
+    equilibrium(L, cfg->equilibrium, rho, rho0, u, feq);
     omegas(cfg, &wp, &wm);
-    for (int q = 0; q < Q; ++q) {
-        int o = OPP[q];
-        double F = 3.0 * W[q] * (C[q][0] * cfg->accel[0] + C[q][1] * cfg->accel[1] + C[q][2] * cfg->accel[2]);
+    for (int q = 0; q < L->Q; ++q) {
+        int o = L->OPP[q];
+        double F = force_term(cfg, L, q);
         double fp = 0.5 * (f[q] + f[o]), fm = 0.5 * (f[q] - f[o]);
         double ep = 0.5 * (feq[q] + feq[o]), em = 0.5 * (feq[q] - feq[o]);
         if (cfg->collision == 0)
@@ -201,9 +251,9 @@ static long cell_index(const oracle_cfg *cfg, int x, int y, int z)
 /* Target of the link from (x,y,z) along c_q.  Returns 0 and the wrapped
  * target cell for a periodic or interior link; returns 1 when the link
  * crosses a wall (half-way bounce-back). */
-static int link_target(const oracle_cfg *cfg, int x, int y, int z, int q, long *target)
+static int link_target(const oracle_cfg *cfg, const lattice *L, int x, int y, int z, int q, long *target)
 {
-    int p[3] = {x + C[q][0], y + C[q][1], z + C[q][2]};
+    int p[3] = {x + L->C[q][0], y + L->C[q][1], z + L->C[q][2]};
     int n[3] = {cfg->nx, cfg->ny, cfg->nz};
     for (int i = 0; i < 3; ++i) {
         if (p[i] < 0 || p[i] >= n[i]) {
@@ -236,31 +286,32 @@ int oracle_max_threads(void)
 /* f(t=0) = feq(rho, u0): the initialisation without non-equilibrium part. */
 void oracle_init(const oracle_cfg *cfg, const double *rho, const double *u, double *f)
 {
-    build_lattice();
+    const lattice *L = cfg_lattice(cfg);
     long n = (long)cfg->nx * cfg->ny * cfg->nz;
     for (long k = 0; k < n; ++k) {
         double uk[3] = {u[k], u[n + k], u[2 * n + k]};
         double rho0 = cfg->rho0_is_rho ? rho[k] : 1.0;
-        equilibrium(cfg->equilibrium, rho[k], rho0, uk, f + k * Q);
+        equilibrium(L, cfg->equilibrium, rho[k], rho0, uk, f + k * L->Q);
     }
 }
 
 /* One time step of Eq. 15: collide every cell, then push along c_q. */
 void oracle_step(const oracle_cfg *cfg, const double *f, double *fnew)
 {
-    build_lattice();
+    const lattice *L = cfg_lattice(cfg);
+    const int Q = L->Q;
     set_threads(cfg);
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < cfg->nz; ++z)
         for (int y = 0; y < cfg->ny; ++y)
             for (int x = 0; x < cfg->nx; ++x) {
                 long k = cell_index(cfg, x, y, z);
-                double fs[Q];
-                collide(cfg, f + k * Q, fs);
+                double fs[QMAX];
+                collide(cfg, L, f + k * Q, fs);
                 for (int q = 0; q < Q; ++q) {
                     long t;
-                    if (link_target(cfg, x, y, z, q, &t))
-                        fnew[k * Q + OPP[q]] = fs[q];
+                    if (link_target(cfg, L, x, y, z, q, &t))
+                        fnew[k * Q + L->OPP[q]] = fs[q];
                     else
                         fnew[t * Q + q] = fs[q];
                 }
@@ -270,11 +321,11 @@ void oracle_step(const oracle_cfg *cfg, const double *f, double *fnew)
 /* rho = sum_q f_q (Eq. 16), u from Eq. 17. */
 void oracle_moments(const oracle_cfg *cfg, const double *f, double *rho, double *u)
 {
-    build_lattice();
+    const lattice *L = cfg_lattice(cfg);
     long n = (long)cfg->nx * cfg->ny * cfg->nz;
     for (long k = 0; k < n; ++k) {
         double r, r0, uk[3];
-        cell_moments(cfg, f + k * Q, &r, &r0, uk);
+        cell_moments(cfg, L, f + k * L->Q, &r, &r0, uk);
         rho[k] = r;
         for (int i = 0; i < 3; ++i) u[i * n + k] = uk[i];
     }
@@ -284,9 +335,10 @@ void oracle_moments(const oracle_cfg *cfg, const double *f, double *rho, double 
 int oracle_run(const oracle_cfg *cfg, const double *rho_in, const double *u_in, int nsteps,
                double *rho_out, double *u_out)
 {
+    const lattice *L = cfg_lattice(cfg);
     long n = (long)cfg->nx * cfg->ny * cfg->nz;
-    double *a = (double *)malloc(sizeof(double) * Q * n);
-    double *b = (double *)malloc(sizeof(double) * Q * n);
+    double *a = (double *)malloc(sizeof(double) * L->Q * n);
+    double *b = (double *)malloc(sizeof(double) * L->Q * n);
     if (!a || !b) { free(a); free(b); return 1; }
     oracle_init(cfg, rho_in, u_in, a);
     for (int s = 0; s < nsteps; ++s) {
@@ -303,22 +355,23 @@ int oracle_run(const oracle_cfg *cfg, const double *rho_in, const double *u_in, 
 
 /* Jacobian J[q][p] = d fs_q / d f_p of the collision of one cell, and the
  * derivatives of fs with respect to omega+ and omega-. */
-static void collide_jacobian(const oracle_cfg *cfg, const double *f, double J[Q][Q],
-                             double dfs_dwp[Q], double dfs_dwm[Q])
+static void collide_jacobian(const oracle_cfg *cfg, const lattice *L, const double *f, double J[][QMAX],
+                             double *dfs_dwp, double *dfs_dwm)
 {
-    double rho, rho0, u[3], feq[Q], du[Q][3], wp, wm, dfeq[Q][Q];
-    cell_moments(cfg, f, &rho, &rho0, u);
-    equilibrium(cfg->equilibrium, rho, rho0, u, feq);
-    equilibrium_du(cfg->equilibrium, u, du);
+    const int Q = L->Q;
+    double rho, rho0, u[3], feq[QMAX], du[QMAX][3], wp, wm, dfeq[QMAX][QMAX];
+    cell_moments(cfg, L, f, &rho, &rho0, u);
+    equilibrium(L, cfg->equilibrium, rho, rho0, u, feq);
+    equilibrium_du(L, cfg->equilibrium, u, du);
     omegas(cfg, &wp, &wm);
     /* d feq_q / d f_p = w_q d rho/d f_p + sum_i d feq_q/d u_i d u_i/d f_p,
      * with d rho / d f_p = 1 and d u_i / d f_p = c_pi (rho0 = 1). */
     for (int q = 0; q < Q; ++q)
         for (int p = 0; p < Q; ++p)
-            dfeq[q][p] = W[q] + du[q][0] * C[p][0] + du[q][1] * C[p][1] + du[q][2] * C[p][2];
+            dfeq[q][p] = L->W[q] + du[q][0] * L->C[p][0] + du[q][1] * L->C[p][1] + du[q][2] * L->C[p][2];
     for (int q = 0; q < Q; ++q) {
-        int o = OPP[q];
-        double F = 3.0 * W[q] * (C[q][0] * cfg->accel[0] + C[q][1] * cfg->accel[1] + C[q][2] * cfg->accel[2]);
+        int o = L->OPP[q];
+        double F = force_term(cfg, L, q);
         for (int p = 0; p < Q; ++p) {
             double dqp = (q == p) ? 1.0 : 0.0, dop = (o == p) ? 1.0 : 0.0;
             double dfp = 0.5 * (dqp + dop), dfm = 0.5 * (dqp - dop);
@@ -336,21 +389,22 @@ static void collide_jacobian(const oracle_cfg *cfg, const double *f, double J[Q]
 int oracle_adjoint_step(const oracle_cfg *cfg, const double *f_t, const double *lam_next,
                         double *lam_t, double *grad_omega)
 {
-    build_lattice();
+    const lattice *L = cfg_lattice(cfg);
+    const int Q = L->Q;
     if (cfg->rho0_is_rho) return 1;
     double gp = 0.0, gm = 0.0;
     for (int z = 0; z < cfg->nz; ++z)
         for (int y = 0; y < cfg->ny; ++y)
             for (int x = 0; x < cfg->nx; ++x) {
                 long k = cell_index(cfg, x, y, z);
-                double J[Q][Q], dwp[Q], dwm[Q], mu[Q];
-                collide_jacobian(cfg, f_t + k * Q, J, dwp, dwm);
+                double J[QMAX][QMAX], dwp[QMAX], dwm[QMAX], mu[QMAX];
+                collide_jacobian(cfg, L, f_t + k * Q, J, dwp, dwm);
                 /* transpose of the push: fs_q(x) went to f_q(x + c_q) or,
                  * through a wall, to f_qbar(x). */
                 for (int q = 0; q < Q; ++q) {
                     long t;
-                    if (link_target(cfg, x, y, z, q, &t))
-                        mu[q] = lam_next[k * Q + OPP[q]];
+                    if (link_target(cfg, L, x, y, z, q, &t))
+                        mu[q] = lam_next[k * Q + L->OPP[q]];
                     else
                         mu[q] = lam_next[t * Q + q];
                 }
@@ -374,21 +428,21 @@ int oracle_adjoint_step(const oracle_cfg *cfg, const double *f_t, const double *
 int oracle_loss_velocity_l2(const oracle_cfg *cfg, const double *f, const double *u_target,
                             double *lam, double *loss)
 {
-    build_lattice();
+    const lattice *L = cfg_lattice(cfg);
     if (cfg->rho0_is_rho) return 1;
     long n = (long)cfg->nx * cfg->ny * cfg->nz;
-    double L = 0.0;
+    double Lsum = 0.0;
     for (long k = 0; k < n; ++k) {
         double r, r0, u[3], g[3];
-        cell_moments(cfg, f + k * Q, &r, &r0, u);
+        cell_moments(cfg, L, f + k * L->Q, &r, &r0, u);
         for (int i = 0; i < 3; ++i) {
             g[i] = u[i] - u_target[i * n + k];
-            L += 0.5 * g[i] * g[i];
+            Lsum += 0.5 * g[i] * g[i];
         }
-        for (int q = 0; q < Q; ++q)
-            lam[k * Q + q] = g[0] * C[q][0] + g[1] * C[q][1] + g[2] * C[q][2];
+        for (int q = 0; q < L->Q; ++q)
+            lam[k * L->Q + q] = g[0] * L->C[q][0] + g[1] * L->C[q][1] + g[2] * L->C[q][2];
     }
-    *loss = L;
+    *loss = Lsum;
     return 0;
 }
 
@@ -397,15 +451,15 @@ int oracle_loss_velocity_l2(const oracle_cfg *cfg, const double *f, const double
 int oracle_adjoint_init_velocity(const oracle_cfg *cfg, const double *u0, const double *lam0,
                                  double *grad_u0)
 {
-    build_lattice();
+    const lattice *L = cfg_lattice(cfg);
     if (cfg->rho0_is_rho) return 1;
     long n = (long)cfg->nx * cfg->ny * cfg->nz;
     for (long k = 0; k < n; ++k) {
-        double uk[3] = {u0[k], u0[n + k], u0[2 * n + k]}, d[Q][3];
-        equilibrium_du(cfg->equilibrium, uk, d);
+        double uk[3] = {u0[k], u0[n + k], u0[2 * n + k]}, d[QMAX][3];
+        equilibrium_du(L, cfg->equilibrium, uk, d);
         for (int i = 0; i < 3; ++i) {
             double s = 0.0;
-            for (int q = 0; q < Q; ++q) s += lam0[k * Q + q] * d[q][i];
+            for (int q = 0; q < L->Q; ++q) s += lam0[k * L->Q + q] * d[q][i];
             grad_u0[i * n + k] = s;
         }
     }
