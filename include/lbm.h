@@ -54,6 +54,7 @@ typedef struct lbm_ctx *lbm_handle;
 
 /* stencil */
 #define LBM_D3Q19 19
+#define LBM_D3Q27 27   /* comparison lattice (Sec. 2.3): A/B step, init, moments, copies */
 
 /* equilibrium (Eq. 14 second-order part / Eq. 22) */
 #define LBM_EQ_STANDARD 0
@@ -120,9 +121,16 @@ const char *lbm_status_string(int status);
  * Host only. */
 int lbm_velocity_set(int *c, double *w, int *opp);
 
+/* The same for a stencil (LBM_D3Q19 or LBM_D3Q27; Q = the stencil value):
+ * c[3*q + i], w[q], opp[q] for q < Q.  Host only. */
+int lbm_velocity_set_of(int stencil, int *c, double *w, int *opp);
+
 /*
  * Creates a handle for an nx * ny * nz lattice (Sec. 2.3 lattice, Eq. 15 update).
- *   stencil      LBM_D3Q19 (others: LBM_EUNSUPPORTED)
+ *   stencil      LBM_D3Q19, or LBM_D3Q27 (standard equilibrium, Eq. 14, for either
+ *                equilibrium choice: the construction of Sec. 3.1 gives Eq. 14
+ *                on D3Q27; A/B pattern only; lbm_reduce, lbm_reduce_noalloc and
+ *                the adjoint return LBM_EUNSUPPORTED)
  *   equilibrium  LBM_EQ_STANDARD (Eq. 14, second order) | LBM_EQ_IMPROVED (Eq. 22)
  *   collision    LBM_SRT (Eq. 15) | LBM_TRT (magic parameter LBM_OPT_TRT_MAGIC)
  *   tau          relaxation time, > 1/2

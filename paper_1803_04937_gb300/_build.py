@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
 SOURCES = ["lbm_step.cu", "lbm_step_f64.cu", "lbm_step_f32.cu", "lbm_step_f16.cu", "lbm_step_bf16.cu",
-           "lbm_fields.cu", "lbm_adjoint.cu", "lbm_api.cu"]
+           "lbm_fields.cu", "lbm_adjoint.cu", "lbm_d3q27.cu", "lbm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

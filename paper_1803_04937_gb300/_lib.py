@@ -12,6 +12,7 @@ from . import _build
 # constants mirrored from include/lbm.h
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSUPPORTED, LBM_ENONFINITE, LBM_ESTATE = range(7)
 LBM_D3Q19 = 19
+LBM_D3Q27 = 27
 EQ_STANDARD, EQ_IMPROVED = 0, 1
 SRT, TRT = 0, 1
 F64, F32, F16S, BF16S = 0, 1, 2, 3
@@ -34,6 +35,7 @@ _SIGS = {
     "lbm_abi_version": (_i, []),
     "lbm_status_string": (ctypes.c_char_p, [_i]),
     "lbm_velocity_set": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
+    "lbm_velocity_set_of": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "lbm_create": (_i, [_i, _i, _i, _i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
     "lbm_destroy": (_i, [_vp]),
     "lbm_set_option": (_i, [_vp, _i, _d]),

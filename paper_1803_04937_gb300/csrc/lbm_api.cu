@@ -15,6 +15,7 @@
 
 struct lbm_ctx {
     int nx = 0, ny = 0, nz = 0;
+    int stencil = LBM_D3Q19;
     int equilibrium = LBM_EQ_IMPROVED, collision = LBM_SRT, precision = LBM_F32;
     double tau = 1.0, magic = 3.0 / 16.0;
     double accel[3] = {0.0, 0.0, 0.0};
@@ -122,6 +123,12 @@ int check_ready(lbm_handle h)
     return LBM_OK;
 }
 
+int d3q19_only(lbm_handle h, const char *what)
+{
+    if (h->stencil == LBM_D3Q19) return LBM_OK;
+    return fail(h, LBM_EUNSUPPORTED, std::string(what) + " is implemented for D3Q19 only");
+}
+
 int check_dtype(lbm_handle h, int dtype)
 {
     if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(h, LBM_EINVAL, "dtype must be LBM_DTYPE_F64 or LBM_DTYPE_F32");
@@ -162,6 +169,16 @@ int lbm_velocity_set(int *c, double *w, int *opp)
     return LBM_OK;
 }
 
+int lbm_velocity_set_of(int stencil, int *c, double *w, int *opp)
+{
+    if (stencil == LBM_D3Q19) return lbm_velocity_set(c, w, opp);
+    if (stencil == LBM_D3Q27) {
+        lbm::velocity_set27(c, w, opp);
+        return LBM_OK;
+    }
+    return LBM_EUNSUPPORTED;
+}
+
 int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collision, double tau, int precision,
                lbm_handle *out)
 {
@@ -169,7 +186,7 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || nz > 65535) return LBM_EINVAL;
     if ((long long)nx * ny * nz >= (1LL << 31)) return LBM_EUNSUPPORTED;
-    if (stencil != LBM_D3Q19) return LBM_EUNSUPPORTED;
+    if (stencil != LBM_D3Q19 && stencil != LBM_D3Q27) return LBM_EUNSUPPORTED;
     if (equilibrium != LBM_EQ_STANDARD && equilibrium != LBM_EQ_IMPROVED) return LBM_EINVAL;
     if (collision != LBM_SRT && collision != LBM_TRT) return LBM_EINVAL;
     if (!(tau > 0.5) || !std::isfinite(tau)) return LBM_EINVAL;
@@ -179,6 +196,7 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
     h->nx = nx;
     h->ny = ny;
     h->nz = nz;
+    h->stencil = stencil;
     h->equilibrium = equilibrium;
     h->collision = collision;
     h->tau = tau;
@@ -225,6 +243,8 @@ int lbm_set_option(lbm_handle h, int key, double v)
         return LBM_OK;
     case LBM_OPT_PATTERN:
         if (v != LBM_PATTERN_AB && v != LBM_PATTERN_AA) return fail(h, LBM_EINVAL, "pattern must be AB or AA");
+        if (v == LBM_PATTERN_AA && h->stencil == LBM_D3Q27)
+            return fail(h, LBM_EUNSUPPORTED, "the AA pattern is D3Q19 only");
         if ((int)v != h->pattern) {
             h->pattern = (int)v;
             h->initialised = false;
@@ -288,7 +308,7 @@ int lbm_get_option(lbm_handle h, int key, double *v)
 int lbm_required_bytes(lbm_handle h, size_t *pdf_bytes, int *n_grids, size_t *scratch_bytes)
 {
     if (!h) return LBM_EINVAL;
-    if (pdf_bytes) *pdf_bytes = (size_t)lbm::Q * (size_t)ncell(h) * elem_size(h->precision);
+    if (pdf_bytes) *pdf_bytes = (size_t)h->stencil * (size_t)ncell(h) * elem_size(h->precision);
     if (n_grids) *n_grids = h->pattern == LBM_PATTERN_AB ? 2 : 1;
     if (scratch_bytes) *scratch_bytes = ((scratch_doubles(h) * sizeof(double) + 255) / 256) * 256;
     return LBM_OK;
@@ -318,7 +338,10 @@ int lbm_init(lbm_handle h, const void *rho, const void *u, int dtype)
     if ((s = check_dtype(h, dtype))) return s;
     if (!u) return fail(h, LBM_EINVAL, "u is NULL");
     h->parity = 0;
-    cudaError_t e = lbm::launch_init(h->precision, layout(h), current(h), rho, u, dtype, geo(h), coll(h), h->stream);
+    cudaError_t e = h->stencil == LBM_D3Q27
+                        ? lbm::launch_init27(h->precision, current(h), rho, u, dtype, geo(h), coll(h), h->stream)
+                        : lbm::launch_init(h->precision, layout(h), current(h), rho, u, dtype, geo(h), coll(h),
+                                           h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_init");
     h->t = 0;
     h->initialised = true;
@@ -339,7 +362,8 @@ int lbm_step(lbm_handle h, int n)
         if (h->pattern == LBM_PATTERN_AB) {
             void *src = current(h);
             void *dst = h->cur ? h->a : h->b;
-            e = lbm::launch_step(h->precision, 0, src, dst, g, c, shape, h->stream);
+            e = h->stencil == LBM_D3Q27 ? lbm::launch_step27(h->precision, src, dst, g, c, shape, h->stream)
+                                        : lbm::launch_step(h->precision, 0, src, dst, g, c, shape, h->stream);
             if (e == cudaSuccess) h->cur ^= 1;
         } else {
             e = lbm::launch_step(h->precision, h->parity ? 2 : 1, h->a, h->a, g, c, shape, h->stream);
@@ -358,7 +382,10 @@ int lbm_moments(lbm_handle h, void *rho, void *u, int dtype)
     if ((s = check_dtype(h, dtype))) return s;
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
     if (!rho && !u) return LBM_OK;
-    cudaError_t e = lbm::launch_moments(h->precision, layout(h), current(h), rho, u, dtype, geo(h), coll(h), h->stream);
+    cudaError_t e = h->stencil == LBM_D3Q27
+                        ? lbm::launch_moments27(h->precision, current(h), rho, u, dtype, geo(h), coll(h), h->stream)
+                        : lbm::launch_moments(h->precision, layout(h), current(h), rho, u, dtype, geo(h), coll(h),
+                                              h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_moments");
     return LBM_OK;
 }
@@ -367,6 +394,7 @@ int lbm_reduce(lbm_handle h, double *out)
 {
     int s = check_ready(h);
     if (s) return s;
+    if ((s = d3q19_only(h, "lbm_reduce"))) return s;
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
     if (!h->scratch) return fail(h, LBM_ESTATE, "lbm_reduce needs a scratch buffer (lbm_bind)");
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
@@ -386,6 +414,7 @@ int lbm_reduce_noalloc(lbm_handle h, double *out)
 {
     int s = check_ready(h);
     if (s) return s;
+    if ((s = d3q19_only(h, "lbm_reduce_noalloc"))) return s;
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
     if ((long long)lbm::reduce_blocks() * 8 + 8 > lbm::reduce_noalloc_capacity_doubles())
@@ -417,7 +446,9 @@ int lbm_get_pdfs(lbm_handle h, void *dst)
     if (!dst) return fail(h, LBM_EINVAL, "dst is NULL");
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
     if (dst == h->a || (h->b && dst == h->b)) return fail(h, LBM_EINVAL, "dst must not be a bound grid");
-    cudaError_t e = lbm::launch_get_pdfs(h->precision, layout(h), current(h), dst, geo(h), h->stream);
+    cudaError_t e = h->stencil == LBM_D3Q27
+                        ? lbm::launch_get27(h->precision, current(h), dst, geo(h), h->stream)
+                        : lbm::launch_get_pdfs(h->precision, layout(h), current(h), dst, geo(h), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_pdfs");
     return LBM_OK;
 }
@@ -429,7 +460,9 @@ int lbm_set_pdfs(lbm_handle h, const void *src)
     if (!src) return fail(h, LBM_EINVAL, "src is NULL");
     if (src == h->a || (h->b && src == h->b)) return fail(h, LBM_EINVAL, "src must not be a bound grid");
     h->parity = 0;
-    cudaError_t e = lbm::launch_set_pdfs(h->precision, layout(h), current(h), src, geo(h), h->stream);
+    cudaError_t e = h->stencil == LBM_D3Q27
+                        ? lbm::launch_set27(h->precision, current(h), src, geo(h), h->stream)
+                        : lbm::launch_set_pdfs(h->precision, layout(h), current(h), src, geo(h), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_pdfs");
     h->t = 0;
     h->initialised = true;
@@ -440,6 +473,7 @@ int lbm_adjoint_seed(lbm_handle h, const void *grad_rho, const void *grad_u, int
 {
     int s = check_ready(h);
     if (s) return s;
+    if ((s = d3q19_only(h, "lbm_adjoint_seed"))) return s;
     if ((s = check_dtype(h, dtype))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!grad_u || !lambda) return fail(h, LBM_EINVAL, "grad_u and lambda are required");
@@ -452,6 +486,7 @@ int lbm_adjoint_step(lbm_handle h, const void *state_t, const void *lambda_next,
 {
     int s = check_ready(h);
     if (s) return s;
+    if ((s = d3q19_only(h, "lbm_adjoint_step"))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!state_t || !lambda_next || !lambda_t || !grad_omega) return fail(h, LBM_EINVAL, "null argument");
     if (lambda_next == lambda_t) return fail(h, LBM_EINVAL, "lambda_next and lambda_t must differ");
@@ -467,6 +502,7 @@ int lbm_adjoint_init_velocity(lbm_handle h, const void *rho, const void *u0, int
 {
     int s = check_ready(h);
     if (s) return s;
+    if ((s = d3q19_only(h, "lbm_adjoint_init_velocity"))) return s;
     if ((s = check_dtype(h, dtype))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!u0 || !lambda0 || !grad_u0) return fail(h, LBM_EINVAL, "null argument");

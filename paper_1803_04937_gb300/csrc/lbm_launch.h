@@ -54,6 +54,17 @@ int reduce_noalloc_capacity_doubles();
 cudaError_t launch_reduce_noalloc(int prec, int layout, const void *grid, const Geo &g, const CollBoth &c,
                                   cudaStream_t s, double **result);
 
+// D3Q27 (A/B pattern only): step, init, moments, canonical copies, velocity set.
+cudaError_t launch_step27(int prec, const void *src, void *dst, const Geo &g, const CollBoth &c, LaunchShape s,
+                          cudaStream_t stream);
+cudaError_t launch_init27(int prec, void *grid, const void *rho, const void *u, int dtype, const Geo &g,
+                          const CollBoth &c, cudaStream_t stream);
+cudaError_t launch_moments27(int prec, const void *grid, void *rho, void *u, int dtype, const Geo &g,
+                             const CollBoth &c, cudaStream_t stream);
+cudaError_t launch_get27(int prec, const void *grid, void *dst, const Geo &g, cudaStream_t stream);
+cudaError_t launch_set27(int prec, void *grid, const void *src, const Geo &g, cudaStream_t stream);
+int velocity_set27(int *c, double *w, int *opp);
+
 // Adjoint kernels (see lbm.h).
 int adjoint_blocks(const Geo &g);
 cudaError_t launch_adjoint_seed(int prec, const void *grad_rho, const void *grad_u, int dtype, void *lambda,

@@ -31,14 +31,15 @@ def _field_dtype(t):
     raise TypeError("macroscopic fields must be float64 or float32, got %s" % t.dtype)
 
 
-def velocity_set():
-    """(c[19,3], w[19], opp[19]) in the library's D3Q19 order."""
+def velocity_set(stencil=19):
+    """(c[Q,3], w[Q], opp[Q]) in the library's D3Q19 (default) or D3Q27 order."""
     lib = _lib.load()
-    c = (ctypes.c_int * 57)()
-    w = (ctypes.c_double * 19)()
-    o = (ctypes.c_int * 19)()
-    check(lib.lbm_velocity_set(c, w, o))
-    return (torch.tensor(list(c), dtype=torch.int64).view(19, 3), torch.tensor(list(w), dtype=torch.float64),
+    nq = int(stencil)
+    c = (ctypes.c_int * (3 * nq))()
+    w = (ctypes.c_double * nq)()
+    o = (ctypes.c_int * nq)()
+    check(lib.lbm_velocity_set_of(nq, c, w, o))
+    return (torch.tensor(list(c), dtype=torch.int64).view(nq, 3), torch.tensor(list(w), dtype=torch.float64),
             torch.tensor(list(o), dtype=torch.int64))
 
 
@@ -49,13 +50,14 @@ class Simulation:
     ("standard" = Eq. 14, "improved" = Eq. 22), collision ("srt" | "trt"), tau,
     storage precision ("f64" | "f32" | "f16s" | "bf16s"), TRT magic parameter,
     body force a, half-way bounce-back walls per axis, rho0 mode and
-    propagation pattern ("ab" | "aa").  Work is enqueued on ``stream`` (default:
-    torch's current stream on ``device``).
+    propagation pattern ("ab" | "aa").  ``stencil=27`` selects the D3Q27
+    comparison lattice (A/B pattern, standard equilibrium).  Work is enqueued on
+    ``stream`` (default: torch's current stream on ``device``).
     """
 
     def __init__(self, nx, ny, nz, equilibrium="improved", collision="srt", tau=0.8, precision="f32",
                  trt_magic=3.0 / 16.0, force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False,
-                 pattern="ab", device="cuda", stream=None, block=None, cells_x=None):
+                 pattern="ab", device="cuda", stream=None, block=None, cells_x=None, stencil=19):
         self._lib = lib = _lib.load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.device = torch.device(device)
@@ -64,7 +66,8 @@ class Simulation:
         self.precision = _PRECISION[precision]
         self.storage_dtype = _STORAGE_DTYPE[self.precision]
         h = ctypes.c_void_p()
-        check(lib.lbm_create(self.nx, self.ny, self.nz, _lib.LBM_D3Q19, _EQ[equilibrium], _COLL[collision],
+        self.stencil = int(stencil)
+        check(lib.lbm_create(self.nx, self.ny, self.nz, self.stencil, _EQ[equilibrium], _COLL[collision],
                              float(tau), self.precision, ctypes.byref(h)))
         self._h = h
         self._set(_lib.OPT_TRT_MAGIC, trt_magic)
@@ -85,7 +88,7 @@ class Simulation:
         scratch_bytes = ctypes.c_size_t()
         check(lib.lbm_required_bytes(h, ctypes.byref(pdf_bytes), ctypes.byref(ngrids), ctypes.byref(scratch_bytes)), h)
         self.pdf_bytes = pdf_bytes.value
-        shape = (19, self.nz, self.ny, self.nx)
+        shape = (self.stencil, self.nz, self.ny, self.nx)
         self.grids = [torch.empty(shape, dtype=self.storage_dtype, device=self.device) for _ in range(ngrids.value)]
         self.scratch = torch.zeros(scratch_bytes.value // 8, dtype=torch.float64, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -155,8 +158,8 @@ class Simulation:
         return t.value
 
     def get_pdfs(self):
-        """Canonical copy f_q - w_q as [19, nz, ny, nx] in storage precision."""
-        out = torch.empty((19,) + self.shape, dtype=self.storage_dtype, device=self.device)
+        """Canonical copy f_q - w_q as [Q, nz, ny, nx] in storage precision."""
+        out = torch.empty((self.stencil,) + self.shape, dtype=self.storage_dtype, device=self.device)
         check(self._lib.lbm_get_pdfs(self._h, _ptr(out)), self._h)
         return out
 

@@ -10,9 +10,10 @@ COLL = {"srt": oracle.SRT, "trt": oracle.TRT}
 
 
 def oracle_config(nx, ny, nz, equilibrium="improved", collision="srt", tau=0.8, trt_magic=3 / 16,
-                  force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False, **_):
+                  force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False, stencil=19, **_):
     return oracle.Config(nx, ny, nz, equilibrium=EQ[equilibrium], collision=COLL[collision], tau=tau,
-                         trt_magic=trt_magic, accel=tuple(force), walls=tuple(walls), rho0_is_rho=rho0_is_rho)
+                         trt_magic=trt_magic, accel=tuple(force), walls=tuple(walls), rho0_is_rho=rho0_is_rho,
+                         stencil=stencil)
 
 
 def random_fields(shape, seed, amp=0.05, drho=0.02):
@@ -23,11 +24,11 @@ def random_fields(shape, seed, amp=0.05, drho=0.02):
     return torch.from_numpy(rho), torch.from_numpy(u)
 
 
-def gpu_to_oracle_order():
+def gpu_to_oracle_order(stencil=19):
     """perm[q_oracle] = q_gpu with equal velocity vectors."""
     from paper_1803_04937_gb300 import lbm
-    cg, wg, _ = lbm.velocity_set()
-    co, wo, _ = oracle.velocity_set()
+    cg, wg, _ = lbm.velocity_set(stencil)
+    co, wo, _ = oracle.velocity_set(stencil)
     index = {tuple(int(a) for a in v): q for q, v in enumerate(cg.tolist())}
     perm = np.array([index[tuple(int(a) for a in v)] for v in co])
     assert np.allclose(wg.numpy()[perm], wo)
@@ -35,10 +36,10 @@ def gpu_to_oracle_order():
 
 
 def gpu_pdfs_in_oracle_layout(sim):
-    """Canonical GPU populations as f[nz, ny, nx, 19] (unshifted, float64, oracle order)."""
-    g = sim.get_pdfs().double().cpu().numpy()  # [19, nz, ny, nx], shifted
-    _, w, _ = oracle.velocity_set()
-    perm = gpu_to_oracle_order()
+    """Canonical GPU populations as f[nz, ny, nx, Q] (unshifted, float64, oracle order)."""
+    g = sim.get_pdfs().double().cpu().numpy()  # [Q, nz, ny, nx], shifted
+    _, w, _ = oracle.velocity_set(sim.stencil)
+    perm = gpu_to_oracle_order(sim.stencil)
     f = np.moveaxis(g[perm], 0, -1) + w
     return f
 

@@ -43,10 +43,30 @@ def test_abi_version_and_velocity_set(lib):
         assert vel[o[q]] == tuple(-a for a in vel[q])
 
 
+def test_d3q27_velocity_set_and_handle(lib):
+    c = (ctypes.c_int * 81)()
+    w = (ctypes.c_double * 27)()
+    o = (ctypes.c_int * 27)()
+    assert lib.lbm_velocity_set_of(27, c, w, o) == 0
+    vel = [tuple(c[3 * q:3 * q + 3]) for q in range(27)]
+    assert len(set(vel)) == 27 and abs(sum(w) - 1.0) < 1e-15
+    assert all(vel[o[q]] == tuple(-a for a in vel[q]) for q in range(27))
+    assert lib.lbm_velocity_set_of(15, c, w, o) == _lib.LBM_EUNSUPPORTED
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(8, 6, 4, 27, 0, 0, 0.8, 1, ctypes.byref(h)) == 0
+    try:
+        pdf = ctypes.c_size_t()
+        assert lib.lbm_required_bytes(h, ctypes.byref(pdf), None, None) == 0
+        assert pdf.value == 27 * 8 * 6 * 4 * 4
+        assert lib.lbm_set_option(h, _lib.OPT_PATTERN, 1) == _lib.LBM_EUNSUPPORTED
+    finally:
+        lib.lbm_destroy(h)
+
+
 def test_create_validates_arguments_on_host(lib):
     h = ctypes.c_void_p()
     assert lib.lbm_create(0, 4, 4, 19, 1, 0, 0.8, 1, ctypes.byref(h)) == _lib.LBM_EINVAL
-    assert lib.lbm_create(4, 4, 4, 27, 1, 0, 0.8, 1, ctypes.byref(h)) == _lib.LBM_EUNSUPPORTED
+    assert lib.lbm_create(4, 4, 4, 15, 1, 0, 0.8, 1, ctypes.byref(h)) == _lib.LBM_EUNSUPPORTED
     assert lib.lbm_create(4, 4, 4, 19, 1, 0, 0.5, 1, ctypes.byref(h)) == _lib.LBM_EINVAL
     assert lib.lbm_create(4, 4, 4, 19, 1, 0, 0.8, 9, ctypes.byref(h)) == _lib.LBM_EINVAL
     assert lib.lbm_create(2048, 1024, 1024, 19, 1, 0, 0.8, 1, ctypes.byref(h)) == _lib.LBM_EUNSUPPORTED

@@ -62,7 +62,7 @@ def test_clock_summary_flags_throttle_reasons():
 
 
 def test_traffic_figure_is_dropped_when_the_kernel_source_changed(tmp_path, monkeypatch):
-    val, sha = bench.read_traffic("k_step_ab<f32>")
+    val, sha = bench.read_traffic("k_ab1<f32>")
     # the committed figure either matches the current source (a number) or is stale (None, current sha)
     assert (val is None and sha) or (val is not None and 100 < val < 200)
     assert bench.read_traffic("no_such_kernel") == (None, None)

@@ -1,0 +1,84 @@
+"""The D3Q27 comparison lattice on the GPU (Sec. 2.3; standard equilibrium,
+which the construction of Sec. 3.1 gives on D3Q27): parity with the FP64
+oracle's D3Q27 step, the paper's duct result for D3Q27 (no transverse
+currents, Sec. 5.1), and unsupported calls failing cleanly."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._helpers import gpu_pdfs_in_oracle_layout, oracle_config, random_fields, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(collision="srt", tau=0.8),
+    dict(collision="trt", tau=0.6, force=(2e-4, -1e-4, 5e-5)),
+    dict(collision="srt", tau=0.7, walls=(True, False, True), force=(1e-4, 0, 0)),
+    dict(collision="trt", tau=0.9, walls=(True, True, True)),
+    dict(collision="srt", tau=1.2, rho0_is_rho=True, force=(1e-4, 2e-4, 0)),
+]
+
+
+@pytest.mark.parametrize("precision,tol,pdf_tol", [("f64", 1e-12, 1e-13), ("f32", 1e-5, 1e-6)])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_d3q27_step_matches_oracle(case, precision, tol, pdf_tol):
+    from paper_1803_04937_gb300.lbm import Simulation
+    kw = CASES[case]
+    shape = (5, 9, 37)
+    rho, u = random_fields(shape, seed=300 + case)
+    sim = Simulation(37, 9, 5, precision=precision, stencil=27, equilibrium="standard", **kw)
+    sim.init(rho.cuda(), u.cuda())
+    sim.step(6)
+    r_g, u_g = (t.cpu().numpy() for t in sim.moments())
+    cfg = oracle_config(37, 9, 5, stencil=27, equilibrium="standard", **kw)
+    f_o = oracle.step(cfg, oracle.init(cfg, rho.numpy(), u.numpy()), 6)
+    r_o, u_o = oracle.moments(cfg, f_o)
+    assert rel_maxnorm(u_g, u_o) < tol
+    assert np.abs(r_g - r_o).max() < tol
+    assert np.abs(gpu_pdfs_in_oracle_layout(sim) - f_o).max() < pdf_tol
+
+
+def test_d3q27_duct_has_no_spurious_currents():
+    from paper_1803_04937_gb300 import inputs
+    from paper_1803_04937_gb300.lbm import Simulation
+    D, tau = 24, 1.0
+    nu = (tau - 0.5) / 3
+    a = 10 * nu * nu / (0.2947 * D * (D / 2) ** 2)
+    sim = Simulation(2, D, D, precision="f64", stencil=27, equilibrium="standard", tau=tau, force=(a, 0, 0),
+                     walls=(False, True, True))
+    rho, u = inputs.rest(2, D, D, device="cuda")
+    sim.init(rho, u)
+    sim.step(int(8 * D * D / (math.pi ** 2 * nu)) + 500)
+    _, ug = sim.moments()
+    ratio = float(ug[1:].abs().max() / ug[0].abs().max())
+    print("duct D=%d D3Q27: max|u_yz|/max|u_x| = %.3e" % (D, ratio))
+    assert ratio < 1e-13
+
+
+def test_d3q27_uniform_flow_keeps_momentum_in_fp32():
+    from paper_1803_04937_gb300.lbm import Simulation
+    n = 16
+    u = torch.zeros((3, n, n, n), dtype=torch.float64)
+    u[0], u[1], u[2] = 0.1, -0.05, 0.02
+    sim = Simulation(n, n, n, precision="f32", stencil=27, collision="srt", tau=0.55)
+    sim.init(None, u.cuda())
+    sim.step(2000)
+    _, ug = sim.moments()
+    err = float((ug.cpu() - u).abs().max() / 0.1)
+    print("D3Q27 uniform flow FP32, 2000 steps: %.2e" % err)
+    assert err < 2e-6
+
+
+def test_d3q27_unsupported_calls_fail_cleanly():
+    from paper_1803_04937_gb300 import _lib
+    from paper_1803_04937_gb300.lbm import Simulation
+    sim = Simulation(8, 8, 8, stencil=27)
+    sim.init(None, torch.zeros((3, 8, 8, 8), dtype=torch.float64, device="cuda"))
+    with pytest.raises(_lib.LBMError) as e:
+        sim.reduce()
+    assert e.value.status == _lib.LBM_EUNSUPPORTED
+    with pytest.raises(_lib.LBMError):
+        Simulation(8, 8, 8, stencil=27, pattern="aa")
