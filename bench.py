@@ -195,12 +195,12 @@ def time_steps(sim, steps, warmup):
     return e0.elapsed_time(e1) * 1e-3 / steps
 
 
-def make_sim(args, n, precision=None, pattern=None, collision=None, equilibrium=None, device="cuda"):
+def make_sim(args, n, precision=None, pattern=None, collision=None, equilibrium=None, device="cuda", stencil=19):
     from paper_1803_04937_gb300.lbm import Simulation
     block = tuple(int(x) for x in args.block.split(",")) if args.block else None
     sim = Simulation(n, n, n, equilibrium=equilibrium or args.equilibrium, collision=collision or args.collision,
                      tau=args.tau, precision=precision or args.precision, pattern=pattern or args.pattern,
-                     device=device, block=block, cells_x=args.cells_x)
+                     device=device, block=block, cells_x=args.cells_x, stencil=stencil)
     rho, u = shear_workload(n, n, n, device)
     sim.init(rho, u.float() if (precision or args.precision) != "f64" else u)
     del rho, u
@@ -212,7 +212,8 @@ def variant_mlups(args, n, **kw):
     sim = make_sim(args, n, **kw)
     t = time_steps(sim, 400, 10)
     prec = kw.get("precision") or args.precision
-    out = {"mlups": n ** 3 / t / 1e6, "gbs": BYTES_PER_LUP[prec] * n ** 3 / t / 1e9}
+    bpl = BYTES_PER_LUP[prec] * kw.get("stencil", 19) // 19
+    out = {"mlups": n ** 3 / t / 1e6, "gbs": bpl * n ** 3 / t / 1e9}
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -439,10 +440,13 @@ def run_native(args):
         variants["aa_f16s"] = variant_mlups(args, n, pattern="aa", precision="f16s")
         variants["trt_" + args.precision] = variant_mlups(args, n, collision="trt")
         variants["standard_" + args.precision] = variant_mlups(args, n, equilibrium="standard")
+        variants["d3q27_" + args.precision] = variant_mlups(args, n, equilibrium="standard", stencil=27)
         for k, v in variants.items():
             v["frac"] = v["gbs"] / peak
         variants["f16s"]["speedup_vs_main"] = variants["f16s"]["mlups"] / value
         variants["bf16s"]["speedup_vs_main"] = variants["bf16s"]["mlups"] / value
+        variants["d3q27_" + args.precision]["d3q19_speedup_over_d3q27"] = value / variants["d3q27_" + args.precision][
+            "mlups"]
         line["variants"] = variants
         line["adjoint"] = adjoint_ratio(args)
     elif rank == 0:
