@@ -9,7 +9,8 @@ Contents
 * ``lbm_oracle.c`` (wrapped here through ctypes): the lattice (Sec. 2.3), the
   standard equilibrium (Eq. 14, second order) and the improved D3Q19-I
   equilibrium (Eq. 22), the update of Eq. 15 with the Buick-Greated force and
-  the velocity shift of Eq. 17, a TRT variant, periodic and half-way
+  the velocity shift of Eq. 17, a TRT variant, an MRT variant in the monomial
+  moment space with Maxwellian equilibrium moments (Sec. 3.2-3.3), periodic and half-way
   bounce-back boundaries (Sec. 5.1), and the adjoint of one step.
 * ``construction.py``: the moment-matching construction of Sec. 3.1-3.2 in
   exact rational arithmetic.
@@ -40,6 +41,7 @@ class _Cfg(ctypes.Structure):
         ("tau", ctypes.c_double), ("trt_magic", ctypes.c_double),
         ("accel", ctypes.c_double * 3),
         ("stencil", ctypes.c_int),
+        ("omega_bulk", ctypes.c_double), ("omega_4", ctypes.c_double),
     ]
 
 
@@ -83,7 +85,7 @@ def _f64(a):
 
 
 STANDARD, IMPROVED = 0, 1
-SRT, TRT = 0, 1
+SRT, TRT, MRT = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -93,7 +95,7 @@ class Config:
     ny: int
     nz: int
     equilibrium: int = IMPROVED      # STANDARD (Eq. 14) or IMPROVED (Eq. 22)
-    collision: int = SRT             # SRT (Eq. 15) or TRT
+    collision: int = SRT             # SRT (Eq. 15), TRT or MRT (Sec. 3.2-3.3)
     tau: float = 0.8
     trt_magic: float = 3.0 / 16.0
     accel: tuple = (0.0, 0.0, 0.0)   # body force a (Buick-Greated, Sec. 2.3)
@@ -101,6 +103,8 @@ class Config:
     rho0_is_rho: bool = False        # rho0 = 1 (paper's choice) or rho0 = rho
     nthreads: int = 0                # OpenMP threads for oracle_step (0: default)
     stencil: int = 19                # 19 (D3Q19) or 27 (D3Q27, standard equilibrium)
+    omega_bulk: float = 1.0          # MRT: rate of the trace of the second-order moments
+    omega_4: float = 1.0             # MRT: rate of the even moments of order >= 4
 
     @property
     def shape(self):
@@ -127,6 +131,8 @@ class Config:
         c.tau = float(self.tau)
         c.trt_magic = float(self.trt_magic)
         c.stencil = int(self.stencil)
+        c.omega_bulk = float(self.omega_bulk)
+        c.omega_4 = float(self.omega_4)
         return c
 
 
@@ -233,7 +239,7 @@ def adjoint_step(cfg: Config, f_t, lam_next):
     g = np.zeros(2)
     c = cfg._c()
     if lib.oracle_adjoint_step(ctypes.byref(c), _dp(f_t), _dp(lam_next), _dp(lam), _dp(g)) != 0:
-        raise ValueError("adjoint requires rho0 = 1")
+        raise ValueError("adjoint requires rho0 = 1 and SRT or TRT")
     return lam, g
 
 

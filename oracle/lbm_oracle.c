@@ -25,6 +25,15 @@
  *     antisymmetric parts relax with omega+ = 1/tau and omega- = 1/tau-,
  *     (tau+ - 1/2)(tau- - 1/2) = Lambda; the force is odd in c and takes
  *     (1 - omega-/2).  With omega- = omega+ this is Eq. 15 exactly.
+ *   - MRT (Sec. 3.2-3.3): the populations are mapped to the monomial moments
+ *     xi_x^e0 xi_y^e1 xi_z^e2, e_i in {0,1,2} (on D3Q19 without the eight of
+ *     Eq. 21), relaxed there against the moments of the Maxwellian truncated
+ *     at second order in u (D3Q19-I; for D3Q19-S against the moments of the
+ *     discrete equilibrium Eq. 14), and mapped back with the inverse moment
+ *     matrix.  Rates: odd orders omega- (as TRT), the deviatoric part of the
+ *     second-order block omega+, its trace omega_bulk, even orders >= 4
+ *     omega_4; the force enters as (I - S/2) M F.  The paper fixes none of the
+ *     rates; with omega_bulk = omega_4 = omega+ this is TRT exactly.
  *   - boundaries: periodic, or half-way bounce-back walls at both ends of an
  *     axis (Sec. 5.1): a population whose link leaves the domain through a
  *     wall returns to its own cell reversed, f_qbar(x, t+1) = f*_q(x, t).
@@ -33,7 +42,7 @@
  * The adjoint (reverse-mode derivative of one step; not in the paper) is
  * written as the transpose of the explicitly assembled QxQ Jacobian of the
  * collision, composed with the transpose of the streaming permutation.  It
- * supports rho0 = 1 only.
+ * supports rho0 = 1 and SRT/TRT only.
  */
 #include <math.h>
 #include <stddef.h>
@@ -49,7 +58,7 @@
 typedef struct {
     int nx, ny, nz;
     int equilibrium;   /* 0: standard D3Q19-S, 1: improved D3Q19-I */
-    int collision;     /* 0: SRT, 1: TRT */
+    int collision;     /* 0: SRT, 1: TRT, 2: MRT */
     int rho0_is_rho;   /* 0: rho0 = 1, 1: rho0 = rho */
     int wall[3];       /* 1: half-way bounce-back walls at both ends of axis */
     int nthreads;      /* OpenMP threads (<= 0: library default) */
@@ -57,6 +66,8 @@ typedef struct {
     double trt_magic;  /* Lambda = (tau+ - 1/2)(tau- - 1/2) */
     double accel[3];   /* body force a */
     int stencil;       /* 19 (D3Q19, default when 0) or 27 (D3Q27) */
+    double omega_bulk; /* MRT: rate of the trace of the second-order moments */
+    double omega_4;    /* MRT: rate of the even moments of order >= 4 */
 } oracle_cfg;
 
 /* A velocity set: Q velocities C, weights W, opposite index OPP. */
@@ -93,12 +104,16 @@ static void build_one(lattice *L, int maxnorm)
                 L->OPP[a] = b;
 }
 
+static void build_bases(void);
+
+/* Built once, before any OpenMP region uses the tables. */
 static void build_lattice(void)
 {
     if (built) return;
     build_one(&D3Q19, 2);
     build_one(&D3Q27, 3);
     built = 1;
+    build_bases();
 }
 
 static const lattice *lattice_of(int stencil)
@@ -195,7 +210,7 @@ static const lattice *cfg_lattice(const oracle_cfg *cfg) { return lattice_of(cfg
 static void omegas(const oracle_cfg *cfg, double *wp, double *wm)
 {
     *wp = 1.0 / cfg->tau;
-    if (cfg->collision == 1) {
+    if (cfg->collision == 1 || cfg->collision == 2) {
         double tau_minus = 0.5 + cfg->trt_magic / (cfg->tau - 0.5);
         *wm = 1.0 / tau_minus;
     } else {
@@ -224,9 +239,182 @@ static double force_term(const oracle_cfg *cfg, const lattice *L, int q)
     return 3.0 * L->W[q] * (c[0] * cfg->accel[0] + c[1] * cfg->accel[1] + c[2] * cfg->accel[2]);
 }
 
-/* Post-collision populations of one cell (Eq. 15, or its TRT split). */
+/* ---------------- MRT in moment space (Sec. 3.2, 3.3) ---------------- */
+
+/* The monomial moments of a stencil: exponents E[k] and the moment matrix
+ * M[k][q] = prod_i c_qi^E[k][i], with its inverse (Gauss-Jordan elimination
+ * with partial pivoting; the matrix is invertible by construction, Sec. 3.2). */
+typedef struct {
+    int K;
+    int E[QMAX][3];
+    double M[QMAX][QMAX], Minv[QMAX][QMAX];
+} moment_basis;
+
+static moment_basis BASIS19, BASIS27;
+
+/* The eight moments Eq. 21 drops for D3Q19. */
+static int dropped_on_d3q19(const int e[3])
+{
+    int n1 = 0, n2 = 0;
+    for (int i = 0; i < 3; ++i) {
+        n1 += e[i] == 1;
+        n2 += e[i] == 2;
+    }
+    /* (1,2,2) and permutations, (1,1,2) and permutations, (1,1,1), (2,2,2) */
+    return (n1 == 1 && n2 == 2) || (n1 == 2 && n2 == 1) || n1 == 3 || n2 == 3;
+}
+
+static double ipow(int c, int e)
+{
+    double r = 1.0;
+    for (int k = 0; k < e; ++k) r *= c;
+    return r;
+}
+
+static void invert(int n, double A[][QMAX], double X[][QMAX])
+{
+    double W[QMAX][2 * QMAX];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) W[r][c] = c < n ? A[r][c] : (c - n == r ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(W[r][col]) > fabs(W[piv][col])) piv = r;
+        if (piv != col)
+            for (int c = 0; c < 2 * n; ++c) {
+                double t = W[col][c]; W[col][c] = W[piv][c]; W[piv][c] = t;
+            }
+        double d = W[col][col];
+        for (int c = 0; c < 2 * n; ++c) W[col][c] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            double m = W[r][col];
+            if (m != 0.0)
+                for (int c = 0; c < 2 * n; ++c) W[r][c] -= m * W[col][c];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) X[r][c] = W[r][n + c];
+}
+
+static void build_basis(moment_basis *B, const lattice *L)
+{
+    int k = 0;
+    for (int e0 = 0; e0 <= 2; ++e0)
+        for (int e1 = 0; e1 <= 2; ++e1)
+            for (int e2 = 0; e2 <= 2; ++e2) {
+                int e[3] = {e0, e1, e2};
+                if (L->Q == 19 && dropped_on_d3q19(e)) continue;
+                for (int i = 0; i < 3; ++i) B->E[k][i] = e[i];
+                for (int q = 0; q < L->Q; ++q)
+                    B->M[k][q] = ipow(L->C[q][0], e0) * ipow(L->C[q][1], e1) * ipow(L->C[q][2], e2);
+                ++k;
+            }
+    B->K = k;
+    invert(k, B->M, B->Minv);
+}
+
+static void build_bases(void)
+{
+    build_basis(&BASIS19, &D3Q19);
+    build_basis(&BASIS27, &D3Q27);
+}
+
+static const moment_basis *basis_of(const lattice *L)
+{
+    return L->Q == 27 ? &BASIS27 : &BASIS19;
+}
+
+/* Moment xi^e of the continuous Maxwellian (Eq. 6, c_s^2 = 1/3) truncated at
+ * second order in u, with rho on the u-free part and rho0 on the rest (Table
+ * 1).  The 1D factors are 1, u, u^2 + 1/3; their product is expanded by
+ * degree in u and cut after degree 2. */
+static double maxwellian_moment(const int e[3], double rho, double rho0, const double u[3])
+{
+    double P[7] = {1.0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        double fac[3] = {0, 0, 0};
+        if (e[i] == 0) fac[0] = 1.0;
+        else if (e[i] == 1) fac[1] = u[i];
+        else { fac[0] = 1.0 / 3.0; fac[2] = u[i] * u[i]; }
+        double R[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < 7; ++a)
+            for (int b = 0; b < 3 && a + b < 7; ++b) R[a + b] += P[a] * fac[b];
+        for (int a = 0; a < 7; ++a) P[a] = R[a];
+    }
+    return rho * P[0] + rho0 * (P[1] + P[2]);
+}
+
+/* Relaxation matrix S in moment space (rates as described at the top). */
+static void mrt_rates(const oracle_cfg *cfg, const moment_basis *B, double S[][QMAX])
+{
+    double wp, wm;
+    omegas(cfg, &wp, &wm);
+    for (int k = 0; k < B->K; ++k)
+        for (int l = 0; l < B->K; ++l) S[k][l] = 0.0;
+    for (int k = 0; k < B->K; ++k) {
+        const int *e = B->E[k];
+        int order = e[0] + e[1] + e[2];
+        int diag2 = order == 2 && (e[0] == 2 || e[1] == 2 || e[2] == 2);
+        if (order % 2 == 1) S[k][k] = wm;
+        else if (order == 0) S[k][k] = wp;
+        else if (order == 2 && !diag2) S[k][k] = wp;
+        else if (order == 2) {
+            /* xi_a^2 block: deviator at omega+, trace at omega_bulk */
+            for (int l = 0; l < B->K; ++l) {
+                const int *g = B->E[l];
+                if (g[0] + g[1] + g[2] == 2 && (g[0] == 2 || g[1] == 2 || g[2] == 2))
+                    S[k][l] = wp * ((k == l ? 1.0 : 0.0) - 1.0 / 3.0) + cfg->omega_bulk / 3.0;
+            }
+        } else S[k][k] = cfg->omega_4;
+    }
+}
+
+/* Post-collision populations of one cell, MRT:
+ * fs = f - M^-1 [ S (M f - m_eq) - (I - S/2) M F ]. */
+static void collide_mrt(const oracle_cfg *cfg, const lattice *L, const double *f, double *fs)
+{
+    const moment_basis *B = basis_of(L);
+    const int K = B->K;
+    double rho, rho0, u[3], S[QMAX][QMAX], m[QMAX], meq[QMAX], mF[QMAX], r[QMAX];
+    cell_moments(cfg, L, f, &rho, &rho0, u);
+    mrt_rates(cfg, B, S);
+    double feq[QMAX], F[QMAX];
+    equilibrium(L, 0, rho, rho0, u, feq);
+    for (int q = 0; q < L->Q; ++q) F[q] = force_term(cfg, L, q);
+    for (int k = 0; k < K; ++k) {
+        m[k] = mF[k] = 0.0;
+        double mS = 0.0;
+        for (int q = 0; q < L->Q; ++q) {
+            m[k] += B->M[k][q] * f[q];
+            mF[k] += B->M[k][q] * F[q];
+            mS += B->M[k][q] * feq[q];
+        }
+        /* improved: Maxwellian moments (Sec. 3.2); standard: moments of Eq. 14 */
+        meq[k] = cfg->equilibrium == 1 ? maxwellian_moment(B->E[k], rho, rho0, u) : mS;
+    }
+    for (int k = 0; k < K; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int l = 0; l < K; ++l) {
+            a += S[k][l] * (m[l] - meq[l]);
+            b += S[k][l] * mF[l];
+        }
+        r[k] = a - (mF[k] - 0.5 * b);
+    }
+    for (int q = 0; q < L->Q; ++q) {
+        double d = 0.0;
+        for (int k = 0; k < K; ++k) d += B->Minv[q][k] * r[k];
+        fs[q] = f[q] - d;
+    }
+}
+
+/* Post-collision populations of one cell (Eq. 15, its TRT split, or MRT). */
 static void collide(const oracle_cfg *cfg, const lattice *L, const double *f, double *fs)
 {
+    if (cfg->collision == 2) {
+        collide_mrt(cfg, L, f, fs);
+        return;
+    }
     double rho, rho0, u[3], feq[QMAX], wp, wm;
     cell_moments(cfg, L, f, &rho, &rho0, u);
     equilibrium(L, cfg->equilibrium, rho, rho0, u, feq);
@@ -391,7 +579,7 @@ int oracle_adjoint_step(const oracle_cfg *cfg, const double *f_t, const double *
 {
     const lattice *L = cfg_lattice(cfg);
     const int Q = L->Q;
-    if (cfg->rho0_is_rho) return 1;
+    if (cfg->rho0_is_rho || cfg->collision == 2) return 1;
     double gp = 0.0, gm = 0.0;
     for (int z = 0; z < cfg->nz; ++z)
         for (int y = 0; y < cfg->ny; ++y)
@@ -471,7 +659,7 @@ void oracle_domega_dtau(const oracle_cfg *cfg, double *dwp, double *dwm)
 {
     double tau = cfg->tau;
     *dwp = -1.0 / (tau * tau);
-    if (cfg->collision == 1) {
+    if (cfg->collision == 1 || cfg->collision == 2) {
         double tm = 0.5 + cfg->trt_magic / (tau - 0.5);
         double dtm = -cfg->trt_magic / ((tau - 0.5) * (tau - 0.5));
         *dwm = -dtm / (tm * tm);
