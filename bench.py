@@ -44,7 +44,7 @@ def parse_args(argv=None):
     p.add_argument("--n", type=int, default=256, help="lattice edge (workload is n^3)")
     p.add_argument("--precision", choices=["f64", "f32", "f16s", "bf16s"], default="f32")
     p.add_argument("--pattern", choices=["ab", "aa"], default="ab")
-    p.add_argument("--collision", choices=["srt", "trt"], default="srt")
+    p.add_argument("--collision", choices=["srt", "trt", "mrt"], default="srt")
     p.add_argument("--equilibrium", choices=["standard", "improved"], default="improved")
     p.add_argument("--tau", type=float, default=0.8)
     p.add_argument("--block", type=str, default=None, help="step kernel block 'bx,by'")
@@ -346,7 +346,8 @@ def run_reference(args):
     budget = 90.0  # seconds for warmup + steps
     c = int(max(2, min(32, math.sqrt(rate * budget / (nx * max(1, args.steps + args.warmup))))))
     cfg = oracle.Config(nx, c, c, equilibrium=oracle.IMPROVED if args.equilibrium == "improved" else oracle.STANDARD,
-                        collision=oracle.SRT if args.collision == "srt" else oracle.TRT, tau=args.tau)
+                        collision={"srt": oracle.SRT, "trt": oracle.TRT, "mrt": oracle.MRT}[args.collision],
+                        tau=args.tau)
     rho, u = shear_workload(nx, c, c, "cpu")
     f = oracle.init(cfg, rho.numpy(), u.numpy())
     f = oracle.step(cfg, f, args.warmup)
@@ -408,8 +409,10 @@ def run_native(args):
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LUP[args.precision] * cells / per_launch / 1e9
     cx = args.cells_x or (4 if args.precision in ("f16s", "bf16s") else 1)
+    if args.collision == "mrt":
+        cx = 1  # the MRT step runs one cell per thread
     if args.pattern == "ab":
-        kname = "k_ab%d<%s>" % (cx, args.precision)
+        kname = "k_ab%d<%s>" % (cx, args.precision) + ("[mrt]" if args.collision == "mrt" else "")
     else:
         kname = "k_aa_even%d+k_aa_odd%d<%s>" % (cx, cx, args.precision)
     traffic_per_lup, _ = read_traffic(kname)
@@ -439,6 +442,8 @@ def run_native(args):
         variants["aa_" + args.precision] = variant_mlups(args, n, pattern="aa")
         variants["aa_f16s"] = variant_mlups(args, n, pattern="aa", precision="f16s")
         variants["trt_" + args.precision] = variant_mlups(args, n, collision="trt")
+        variants["mrt_" + args.precision] = variant_mlups(args, n, collision="mrt")
+        variants["mrt_f16s"] = variant_mlups(args, n, collision="mrt", precision="f16s")
         variants["standard_" + args.precision] = variant_mlups(args, n, equilibrium="standard")
         variants["d3q27_" + args.precision] = variant_mlups(args, n, equilibrium="standard", stencil=27)
         for k, v in variants.items():

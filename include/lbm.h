@@ -63,6 +63,18 @@ typedef struct lbm_ctx *lbm_handle;
 /* collision */
 #define LBM_SRT 0
 #define LBM_TRT 1
+/* MRT (Sec. 3.2-3.3, D3Q19 only): relaxation in the moment space of the
+ * monomials xi_x^a xi_y^b xi_z^c (a, b, c in {0,1,2}, without the eight that
+ * Eq. 21 drops), against the Maxwellian's moments truncated at second order
+ * (LBM_EQ_IMPROVED, which equals Eq. 22 in population space) or against the
+ * moments of Eq. 14 (LBM_EQ_STANDARD).  Rates: odd moments omega- (from the
+ * magic parameter, as TRT), deviatoric second-order moments omega+ = 1/tau,
+ * the trace of the second-order moments LBM_OPT_MRT_OMEGA_BULK, the
+ * fourth-order moments LBM_OPT_MRT_OMEGA_4.  Force: (I - S/2) applied in
+ * moment space.  With both extra rates equal to 1/tau it is LBM_TRT.  Not
+ * every pair of rates is linearly stable (e.g. omega_bulk = 1.9 with
+ * omega_4 = 1 at tau = 0.6 is not); the library does not check. */
+#define LBM_MRT 2
 
 /* storage precision of the populations (S = shifted storage f_q - w_q);
  * collision arithmetic is FP64 for LBM_F64 and FP32 otherwise. */
@@ -91,14 +103,18 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_OPT_PATTERN    9  /* LBM_PATTERN_AB (default) or LBM_PATTERN_AA */
 #define LBM_OPT_TAU       10  /* relaxation time tau (> 1/2) */
 #define LBM_OPT_EQUILIBRIUM 11 /* LBM_EQ_STANDARD or LBM_EQ_IMPROVED */
-#define LBM_OPT_COLLISION 12  /* LBM_SRT or LBM_TRT */
+#define LBM_OPT_COLLISION 12  /* LBM_SRT, LBM_TRT or LBM_MRT (D3Q19) */
 #define LBM_OPT_BLOCK_X   13  /* step kernel threads per block along x (tuning) */
 #define LBM_OPT_BLOCK_Y   14  /* ... along y; bx * by <= 256 and a multiple of 32 */
 #define LBM_OPT_CELLS_X   15  /* cells per thread along x in the step kernel: 1; 2 (paired
                                  accesses; nx even, bx a multiple of 32); or 4 (16-bit storage,
                                  A/B pattern, nx a multiple of 4, 128-thread blocks shaped from
                                  nx; otherwise treated as 2).  Default 4 for 16-bit storage, 1
-                                 otherwise. */
+                                 otherwise.  LBM_MRT always runs one cell per thread. */
+#define LBM_OPT_MRT_OMEGA_BULK 16 /* LBM_MRT: rate of the trace of the second-order moments
+                                     (bulk viscosity (2/9)(1/omega - 1/2)); 0 < v < 2, default 1 */
+#define LBM_OPT_MRT_OMEGA_4    17 /* LBM_MRT: rate of the fourth-order moments; 0 < v < 2,
+                                     default 1 */
 
 /* lbm_reduce output slots */
 #define LBM_RED_MASS      0   /* sum_x rho */
@@ -132,7 +148,8 @@ int lbm_velocity_set_of(int stencil, int *c, double *w, int *opp);
  *                on D3Q27; A/B pattern only; lbm_reduce, lbm_reduce_noalloc and
  *                the adjoint return LBM_EUNSUPPORTED)
  *   equilibrium  LBM_EQ_STANDARD (Eq. 14, second order) | LBM_EQ_IMPROVED (Eq. 22)
- *   collision    LBM_SRT (Eq. 15) | LBM_TRT (magic parameter LBM_OPT_TRT_MAGIC)
+ *   collision    LBM_SRT (Eq. 15) | LBM_TRT (magic parameter LBM_OPT_TRT_MAGIC) |
+ *                LBM_MRT (D3Q19 only; LBM_EUNSUPPORTED with LBM_D3Q27)
  *   tau          relaxation time, > 1/2
  *   precision    LBM_F64 | LBM_F32 | LBM_F16S | LBM_BF16S
  * Sizes: each >= 1, nx * ny * nz < 2^31.  Host only (no CUDA call).
@@ -257,6 +274,9 @@ int lbm_set_pdfs(lbm_handle h, const void *src);
  * lbm_adjoint_tau_gradient: dL/dtau = dL/domega+ domega+/dtau +
  *   dL/domega- domega-/dtau for the handle's tau, collision and magic
  *   parameter, from host copies of grad_omega.  Host only.
+ *
+ * The adjoint covers LBM_SRT and LBM_TRT; with LBM_MRT every adjoint entry
+ * point returns LBM_EUNSUPPORTED.
  */
 int lbm_adjoint_seed(lbm_handle h, const void *grad_rho, const void *grad_u, int dtype,
                      void *lambda);

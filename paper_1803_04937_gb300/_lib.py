@@ -14,7 +14,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSUPPORTED, LBM_ENONFINITE, LBM
 LBM_D3Q19 = 19
 LBM_D3Q27 = 27
 EQ_STANDARD, EQ_IMPROVED = 0, 1
-SRT, TRT = 0, 1
+SRT, TRT, MRT = 0, 1, 2
 F64, F32, F16S, BF16S = 0, 1, 2, 3
 DTYPE_F64, DTYPE_F32 = 0, 1
 PATTERN_AB, PATTERN_AA = 0, 1
@@ -22,6 +22,7 @@ OPT_TRT_MAGIC, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = 1, 2, 3, 4
 OPT_WALLS_X, OPT_WALLS_Y, OPT_WALLS_Z = 5, 6, 7
 OPT_RHO0_MODE, OPT_PATTERN, OPT_TAU, OPT_EQUILIBRIUM, OPT_COLLISION = 8, 9, 10, 11, 12
 OPT_BLOCK_X, OPT_BLOCK_Y, OPT_CELLS_X = 13, 14, 15
+OPT_MRT_OMEGA_BULK, OPT_MRT_OMEGA_4 = 16, 17
 RED_MASS, RED_ENERGY, RED_JX, RED_JY, RED_JZ, RED_UMAX, RED_NONFINITE = range(7)
 RED_COUNT = 8
 

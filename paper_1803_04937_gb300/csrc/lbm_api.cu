@@ -18,6 +18,7 @@ struct lbm_ctx {
     int stencil = LBM_D3Q19;
     int equilibrium = LBM_EQ_IMPROVED, collision = LBM_SRT, precision = LBM_F32;
     double tau = 1.0, magic = 3.0 / 16.0;
+    double omega_bulk = 1.0, omega_4 = 1.0;  // MRT only
     double accel[3] = {0.0, 0.0, 0.0};
     int walls[3] = {0, 0, 0};
     int rho0_mode = 0;
@@ -85,6 +86,9 @@ lbm::CollBoth coll(const lbm_ctx *h)
     c.omega_p = 1.0 / h->tau;
     c.omega_m = omega_minus(h);
     c.kappa = h->equilibrium == LBM_EQ_IMPROVED ? 1.0 : 0.0;
+    c.mrt = h->collision == LBM_MRT;
+    c.omega_bulk = c.mrt ? h->omega_bulk : c.omega_p;
+    c.omega_4 = c.mrt ? h->omega_4 : c.omega_p;
     for (int i = 0; i < 3; ++i) c.half_a[i] = 0.5 * h->accel[i];
     // (1 - omega-/2) F_q with F_q = w_q c_q . a / c_s^2 (Buick-Greated), for
     // the first member q = 2k+1 of each opposite pair.
@@ -127,6 +131,12 @@ int d3q19_only(lbm_handle h, const char *what)
 {
     if (h->stencil == LBM_D3Q19) return LBM_OK;
     return fail(h, LBM_EUNSUPPORTED, std::string(what) + " is implemented for D3Q19 only");
+}
+
+int no_mrt(lbm_handle h, const char *what)
+{
+    if (h->collision != LBM_MRT) return LBM_OK;
+    return fail(h, LBM_EUNSUPPORTED, std::string(what) + " supports SRT and TRT only");
 }
 
 int check_dtype(lbm_handle h, int dtype)
@@ -188,7 +198,8 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
     if ((long long)nx * ny * nz >= (1LL << 31)) return LBM_EUNSUPPORTED;
     if (stencil != LBM_D3Q19 && stencil != LBM_D3Q27) return LBM_EUNSUPPORTED;
     if (equilibrium != LBM_EQ_STANDARD && equilibrium != LBM_EQ_IMPROVED) return LBM_EINVAL;
-    if (collision != LBM_SRT && collision != LBM_TRT) return LBM_EINVAL;
+    if (collision != LBM_SRT && collision != LBM_TRT && collision != LBM_MRT) return LBM_EINVAL;
+    if (collision == LBM_MRT && stencil != LBM_D3Q19) return LBM_EUNSUPPORTED;
     if (!(tau > 0.5) || !std::isfinite(tau)) return LBM_EINVAL;
     if (elem_size(precision) == 0) return LBM_EINVAL;
     lbm_ctx *h = new (std::nothrow) lbm_ctx();
@@ -261,8 +272,14 @@ int lbm_set_option(lbm_handle h, int key, double v)
         h->equilibrium = (int)v;
         return LBM_OK;
     case LBM_OPT_COLLISION:
-        if (v != LBM_SRT && v != LBM_TRT) return fail(h, LBM_EINVAL, "bad collision");
+        if (v != LBM_SRT && v != LBM_TRT && v != LBM_MRT) return fail(h, LBM_EINVAL, "bad collision");
+        if (v == LBM_MRT && h->stencil != LBM_D3Q19) return fail(h, LBM_EUNSUPPORTED, "MRT is D3Q19 only");
         h->collision = (int)v;
+        return LBM_OK;
+    case LBM_OPT_MRT_OMEGA_BULK:
+    case LBM_OPT_MRT_OMEGA_4:
+        if (!(v > 0.0 && v < 2.0)) return fail(h, LBM_EINVAL, "MRT rates must lie in (0, 2)");
+        (key == LBM_OPT_MRT_OMEGA_BULK ? h->omega_bulk : h->omega_4) = v;
         return LBM_OK;
     case LBM_OPT_CELLS_X:
         if (v != 1.0 && v != 2.0 && v != 4.0) return fail(h, LBM_EINVAL, "cells per thread must be 1, 2 or 4");
@@ -298,6 +315,8 @@ int lbm_get_option(lbm_handle h, int key, double *v)
     case LBM_OPT_TAU: *v = h->tau; return LBM_OK;
     case LBM_OPT_EQUILIBRIUM: *v = h->equilibrium; return LBM_OK;
     case LBM_OPT_COLLISION: *v = h->collision; return LBM_OK;
+    case LBM_OPT_MRT_OMEGA_BULK: *v = h->omega_bulk; return LBM_OK;
+    case LBM_OPT_MRT_OMEGA_4: *v = h->omega_4; return LBM_OK;
     case LBM_OPT_CELLS_X: *v = h->cells_x; return LBM_OK;
     case LBM_OPT_BLOCK_X: *v = h->bx; return LBM_OK;
     case LBM_OPT_BLOCK_Y: *v = h->by; return LBM_OK;
@@ -474,6 +493,7 @@ int lbm_adjoint_seed(lbm_handle h, const void *grad_rho, const void *grad_u, int
     int s = check_ready(h);
     if (s) return s;
     if ((s = d3q19_only(h, "lbm_adjoint_seed"))) return s;
+    if ((s = no_mrt(h, "lbm_adjoint_seed"))) return s;
     if ((s = check_dtype(h, dtype))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!grad_u || !lambda) return fail(h, LBM_EINVAL, "grad_u and lambda are required");
@@ -487,6 +507,7 @@ int lbm_adjoint_step(lbm_handle h, const void *state_t, const void *lambda_next,
     int s = check_ready(h);
     if (s) return s;
     if ((s = d3q19_only(h, "lbm_adjoint_step"))) return s;
+    if ((s = no_mrt(h, "lbm_adjoint_step"))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!state_t || !lambda_next || !lambda_t || !grad_omega) return fail(h, LBM_EINVAL, "null argument");
     if (lambda_next == lambda_t) return fail(h, LBM_EINVAL, "lambda_next and lambda_t must differ");
@@ -503,6 +524,7 @@ int lbm_adjoint_init_velocity(lbm_handle h, const void *rho, const void *u0, int
     int s = check_ready(h);
     if (s) return s;
     if ((s = d3q19_only(h, "lbm_adjoint_init_velocity"))) return s;
+    if ((s = no_mrt(h, "lbm_adjoint_init_velocity"))) return s;
     if ((s = check_dtype(h, dtype))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!u0 || !lambda0 || !grad_u0) return fail(h, LBM_EINVAL, "null argument");
@@ -515,6 +537,8 @@ int lbm_adjoint_init_velocity(lbm_handle h, const void *rho, const void *u0, int
 int lbm_adjoint_tau_gradient(lbm_handle h, const double *grad_omega, double *dL_dtau)
 {
     if (!h || !grad_omega || !dL_dtau) return LBM_EINVAL;
+    int s = no_mrt(h, "lbm_adjoint_tau_gradient");
+    if (s) return s;
     const double tau = h->tau;
     const double dwp = -1.0 / (tau * tau);
     double dwm = dwp;

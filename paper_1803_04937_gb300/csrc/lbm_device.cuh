@@ -361,6 +361,7 @@ struct Relax {
     R Af, Ae;        // 6 wf, 6 we  (twice the antisymmetric coefficient)
     R half_a[3];     // a / 2
     R force[9];      // (1 - omega- / 2) F_q, q = 2k+1
+    R hb, h4;        // MRT: (omega+ - omega_bulk) / 2, (omega+ - omega_4) / 2
 };
 
 template <typename R>
@@ -389,6 +390,8 @@ static inline Relax<R> to_relax(const CollBoth &c)
     r.Af = R(1) - R(4) * r.Ae;
     for (int i = 0; i < 3; ++i) r.half_a[i] = R(c.half_a[i]);
     for (int i = 0; i < 9; ++i) r.force[i] = R(c.force[i]);
+    r.hb = R(0.5 * (wp - c.omega_bulk));
+    r.h4 = R(0.5 * (wp - c.omega_4));
     return r;
 }
 
@@ -501,6 +504,72 @@ __device__ __forceinline__ void collide_lean(R g[Q], const Relax<R> &p)
     relax_pair<R, RHO0_IS_RHO, 6>(g, e, p);
     relax_pair<R, RHO0_IS_RHO, 7>(g, e, p);
     relax_pair<R, RHO0_IS_RHO, 8>(g, e, p);
+}
+
+// MRT collision (Sec. 3.2-3.3) in population space.  The even part of the
+// non-equilibrium (rest n0 and pair sums ns) has, in the monomial moment basis,
+// the second-order moments P and the fourth-order moments Q_c = sum over the
+// two edge pairs normal to axis c (xi_a^2 xi_b^2, {a,b,c} = {x,y,z}); its
+// zeroth moment is zero.  Relaxing the deviator of P at omega+, the trace
+// T = tr P at omega_bulk and Q at omega_4 equals relaxing everything at
+// omega+ and adding back (omega+ - omega_bulk) times the population vector
+// whose only non-zero moment is that trace (rest -T, faces T/3, edges 0),
+// plus (omega+ - omega_4) times the vector whose only non-zero moments are
+// the Q (rest sum Q, face a Q_a - sum Q, edges normal to c Q_c/2); these are
+// the columns of the inverse moment matrix for those moments.  The odd part
+// relaxes at omega- with the force, exactly as in collide_lean.
+template <typename R, bool RHO0_IS_RHO>
+__device__ __forceinline__ void collide_mrt(R g[Q], const Relax<R> &p)
+{
+    const CellEq<R, RHO0_IS_RHO> e(g, p);
+    R ns[9], na[9];
+    e.template neq<0>(ns[0], na[0]);
+    e.template neq<1>(ns[1], na[1]);
+    e.template neq<2>(ns[2], na[2]);
+    e.template neq<3>(ns[3], na[3]);
+    e.template neq<4>(ns[4], na[4]);
+    e.template neq<5>(ns[5], na[5]);
+    e.template neq<6>(ns[6], na[6]);
+    e.template neq<7>(ns[7], na[7]);
+    e.template neq<8>(ns[8], na[8]);
+    R faces = R(0), Qn[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        if (NORM2(q) == 1) faces += ns[k];
+        else Qn[CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2)] += ns[k];
+    }
+    const R Qsum = (Qn[0] + Qn[1]) + Qn[2];
+    const R T = fma(R(2), Qsum, faces);
+    const R bT = p.hb * T;       // (omega+ - omega_bulk) T / 2
+    const R bQ = p.h4 * Qsum;    // (omega+ - omega_4) sum Q / 2
+    g[0] = fma(-p.wp, g[0] - e.eq0, g[0]) - R(2) * (bT - bQ);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        R corr;  // (omega+ - omega_bulk) B / 2 + (omega+ - omega_4) G / 2 for this pair
+        if (NORM2(q) == 1) {
+            const int a = CX(q) ? 0 : (CY(q) ? 1 : 2);
+            corr = fma(p.h4, Qn[a], bT * R(1.0 / 3.0) - bQ);
+        } else {
+            const int c = CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2);
+            corr = R(0.5) * p.h4 * Qn[c];
+        }
+        const R a1 = fma(p.hp, ns[k], -corr);
+        const R b = fma(p.hm, na[k], -p.force[k]);
+        g[q] = (g[q] - a1) - b;
+        g[q + 1] = (g[q + 1] - a1) + b;
+    }
+}
+
+// Step collision: the lean SRT/TRT update, or MRT.
+template <typename R, bool RHO0_IS_RHO, bool MRT>
+__device__ __forceinline__ void collide_any(R g[Q], const Relax<R> &p)
+{
+    if constexpr (MRT)
+        collide_mrt<R, RHO0_IS_RHO>(g, p);
+    else
+        collide_lean<R, RHO0_IS_RHO>(g, p);
 }
 
 // Shifted equilibrium geq_q = feq_q(rho, u) - w_q for all q (lbm_init).

@@ -20,6 +20,8 @@ struct LaunchShape {
 // Collision constants for both arithmetic types; the launcher picks one.
 struct CollBoth {
     double omega_p, omega_m, kappa;
+    double omega_bulk, omega_4;  // MRT rates (equal to omega_p otherwise)
+    int mrt;                     // 1: MRT collision (one cell per thread)
     double half_a[3];
     double force[9];
     int rho0_is_rho;

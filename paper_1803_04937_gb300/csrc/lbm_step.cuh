@@ -176,7 +176,7 @@ __device__ __forceinline__ void gather1(const Planes<T> &P, const Site<WALLS> &s
     }
 }
 
-template <typename T, bool RHO0, bool WALLS>
+template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
@@ -187,13 +187,13 @@ __global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g
     const Site<WALLS> s(x, y, z, 1, g);
     R f[Q];
     gather1<false>(src, s, f);
-    collide_lean<R, RHO0>(f, p);
+    collide_any<R, RHO0, MRT>(f, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Storage<T>::store(dst.p[q] + s.own + x, f[q]);
 }
 
 // AA even step: own cell only (read plane q, write plane qbar).
-template <typename T, bool RHO0>
+template <typename T, bool RHO0, bool MRT = false>
 __global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Geo g, Relax<type
     R f[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) f[q] = Storage<T>::load(P.p[q] + own);
-    collide_lean<R, RHO0>(f, p);
+    collide_any<R, RHO0, MRT>(f, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Storage<T>::store(P.p[OPP(q)] + own, f[q]);
 }
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Geo g, Relax<type
 // AA odd step: read plane qbar at x - c_q, write plane q at x + c_q (through
 // a wall: read plane q / write plane qbar of the own cell).  Every location is
 // read and written by exactly one thread.
-template <typename T, bool RHO0, bool WALLS>
+template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(256) k_aa_odd1(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_aa_odd1(Planes<T> P, Geo g, Relax<typen
     const Site<WALLS> s(x, y, z, 1, g);
     R f[Q];
     gather1<true>(P, s, f);
-    collide_lean<R, RHO0>(f, p);
+    collide_any<R, RHO0, MRT>(f, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q);
@@ -533,6 +533,18 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
     using R = typename Storage<T>::R;
     const Relax<R> p = to_relax<R>(cb);
     const dim3 block(ls.bx, ls.by, 1);
+    if (cb.mrt) {
+        // MRT: one cell per thread
+        const dim3 grid1((g.nx + ls.bx - 1) / ls.bx, (g.ny + ls.by - 1) / ls.by, g.nz);
+        const Planes<T> D = planes_of<T>(dst, g.ncell);
+        if (kind == 0)
+            k_ab1<T, RHO0, WALLS, true><<<grid1, block, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
+        else if (kind == 1)
+            k_aa_even1<T, RHO0, true><<<grid1, block, 0, stream>>>(D, g, p);
+        else
+            k_aa_odd1<T, RHO0, WALLS, true><<<grid1, block, 0, stream>>>(D, g, p);
+        return cudaGetLastError();
+    }
     const bool quads = sizeof(T) == 2 && kind == 0 && ls.cells_x == 4 && (g.nx % 4) == 0;
     const bool pairs = !quads && ls.cells_x >= 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
     if (quads) {

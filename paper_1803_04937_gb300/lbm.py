@@ -15,7 +15,7 @@ _PRECISION = {"f64": _lib.F64, "f32": _lib.F32, "f16s": _lib.F16S, "bf16s": _lib
 _STORAGE_DTYPE = {_lib.F64: torch.float64, _lib.F32: torch.float32, _lib.F16S: torch.float16,
                   _lib.BF16S: torch.bfloat16}
 _EQ = {"standard": _lib.EQ_STANDARD, "improved": _lib.EQ_IMPROVED}
-_COLL = {"srt": _lib.SRT, "trt": _lib.TRT}
+_COLL = {"srt": _lib.SRT, "trt": _lib.TRT, "mrt": _lib.MRT}
 _PATTERN = {"ab": _lib.PATTERN_AB, "aa": _lib.PATTERN_AA}
 
 
@@ -47,8 +47,10 @@ class Simulation:
     """One D3Q19 lattice on one GPU.
 
     Parameters mirror ``lbm_create`` / ``lbm_set_option``: equilibrium
-    ("standard" = Eq. 14, "improved" = Eq. 22), collision ("srt" | "trt"), tau,
-    storage precision ("f64" | "f32" | "f16s" | "bf16s"), TRT magic parameter,
+    ("standard" = Eq. 14, "improved" = Eq. 22), collision ("srt" | "trt" |
+    "mrt"), tau, storage precision ("f64" | "f32" | "f16s" | "bf16s"), TRT magic
+    parameter (also the odd-moment rate of MRT), the MRT bulk and fourth-order
+    rates ``omega_bulk`` and ``omega_4``,
     body force a, half-way bounce-back walls per axis, rho0 mode and
     propagation pattern ("ab" | "aa").  ``stencil=27`` selects the D3Q27
     comparison lattice (A/B pattern, standard equilibrium).  Work is enqueued on
@@ -57,7 +59,8 @@ class Simulation:
 
     def __init__(self, nx, ny, nz, equilibrium="improved", collision="srt", tau=0.8, precision="f32",
                  trt_magic=3.0 / 16.0, force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False,
-                 pattern="ab", device="cuda", stream=None, block=None, cells_x=None, stencil=19):
+                 pattern="ab", device="cuda", stream=None, block=None, cells_x=None, stencil=19, omega_bulk=1.0,
+                 omega_4=1.0):
         self._lib = lib = _lib.load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.device = torch.device(device)
@@ -71,6 +74,9 @@ class Simulation:
                              float(tau), self.precision, ctypes.byref(h)))
         self._h = h
         self._set(_lib.OPT_TRT_MAGIC, trt_magic)
+        if collision == "mrt":
+            self._set(_lib.OPT_MRT_OMEGA_BULK, omega_bulk)
+            self._set(_lib.OPT_MRT_OMEGA_4, omega_4)
         for i in range(3):
             self._set(_lib.OPT_FORCE_X + i, force[i])
             self._set(_lib.OPT_WALLS_X + i, 1.0 if walls[i] else 0.0)

@@ -6,14 +6,15 @@ import torch
 import oracle
 
 EQ = {"standard": oracle.STANDARD, "improved": oracle.IMPROVED}
-COLL = {"srt": oracle.SRT, "trt": oracle.TRT}
+COLL = {"srt": oracle.SRT, "trt": oracle.TRT, "mrt": oracle.MRT}
 
 
 def oracle_config(nx, ny, nz, equilibrium="improved", collision="srt", tau=0.8, trt_magic=3 / 16,
-                  force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False, stencil=19, **_):
+                  force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False, stencil=19, omega_bulk=1.0,
+                  omega_4=1.0, **_):
     return oracle.Config(nx, ny, nz, equilibrium=EQ[equilibrium], collision=COLL[collision], tau=tau,
                          trt_magic=trt_magic, accel=tuple(force), walls=tuple(walls), rho0_is_rho=rho0_is_rho,
-                         stencil=stencil)
+                         stencil=stencil, omega_bulk=omega_bulk, omega_4=omega_4)
 
 
 def random_fields(shape, seed, amp=0.05, drho=0.02):

@@ -101,3 +101,29 @@ def test_create_validates_arguments_on_host(lib):
         assert abs(d.value - 2 * (-1 / 0.8 ** 2)) < 1e-14
     finally:
         assert lib.lbm_destroy(h) == 0
+
+
+def test_mrt_options_and_refusals_on_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(8, 6, 4, 27, 1, _lib.MRT, 0.8, 1, ctypes.byref(h)) == _lib.LBM_EUNSUPPORTED
+    assert lib.lbm_create(8, 6, 4, 27, 1, _lib.TRT, 0.8, 1, ctypes.byref(h)) == _lib.LBM_OK
+    try:
+        assert lib.lbm_set_option(h, _lib.OPT_COLLISION, _lib.MRT) == _lib.LBM_EUNSUPPORTED
+    finally:
+        lib.lbm_destroy(h)
+    assert lib.lbm_create(8, 6, 4, 19, 1, _lib.MRT, 0.8, 1, ctypes.byref(h)) == _lib.LBM_OK
+    try:
+        v = ctypes.c_double()
+        for key in (_lib.OPT_MRT_OMEGA_BULK, _lib.OPT_MRT_OMEGA_4):
+            assert lib.lbm_get_option(h, key, ctypes.byref(v)) == 0 and v.value == 1.0
+            assert lib.lbm_set_option(h, key, 0.0) == _lib.LBM_EINVAL
+            assert lib.lbm_set_option(h, key, 2.0) == _lib.LBM_EINVAL
+            assert lib.lbm_set_option(h, key, 1.3) == 0
+            assert lib.lbm_get_option(h, key, ctypes.byref(v)) == 0 and v.value == 1.3
+        assert lib.lbm_get_option(h, _lib.OPT_COLLISION, ctypes.byref(v)) == 0 and v.value == _lib.MRT
+        g = (ctypes.c_double * 2)(1.0, 1.0)
+        d = ctypes.c_double()
+        assert lib.lbm_adjoint_tau_gradient(h, g, ctypes.byref(d)) == _lib.LBM_EUNSUPPORTED
+        assert b"SRT and TRT" in lib.lbm_last_error(h)
+    finally:
+        lib.lbm_destroy(h)
