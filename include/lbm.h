@@ -108,7 +108,7 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_OPT_BLOCK_Y   14  /* ... along y; bx * by <= 256 and a multiple of 32 */
 #define LBM_OPT_CELLS_X   15  /* cells per thread along x in the step kernel: 1; 2 (paired
                                  accesses; nx even, bx a multiple of 32); or 4 (16-bit storage,
-                                 A/B pattern, nx a multiple of 4, 128-thread blocks shaped from
+                                 A/B and AA, nx a multiple of 4, 128-thread blocks shaped from
                                  nx; otherwise treated as 2).  Default 4 for 16-bit storage, 1
                                  otherwise.  LBM_MRT always runs one cell per thread. */
 #define LBM_OPT_MRT_OMEGA_BULK 16 /* LBM_MRT: rate of the trace of the second-order moments

@@ -217,7 +217,7 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
         h->by = 256 / h->bx;
     }
     // 16-bit storage needs wide accesses shared by several cells to approach
-    // the bandwidth roofline: four cells per thread (A/B; the AA steps use two)
+    // the bandwidth roofline: four cells per thread (A/B and AA)
     h->cells_x = (precision == LBM_F16S || precision == LBM_BF16S) ? 4 : 1;
     *out = h;
     return LBM_OK;

@@ -99,6 +99,25 @@ struct Site {
     }
 };
 
+// An in-place step writes the locations it has read; left alone, the compiler
+// keeps the 19 load addresses (64-bit each) alive through the collisions to
+// reuse them for the stores, and spills.  Passing the offsets through an
+// empty asm statement hides that equality, so the store addresses are formed
+// again from the kernel-parameter base pointers after the collisions.
+__device__ __forceinline__ void opaque(int &v) { asm volatile("" : "+r"(v)); }
+template <bool WALLS>
+__device__ __forceinline__ void opaque(Site<WALLS> &s)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) opaque(s.row[a][b]);
+    opaque(s.own);
+    opaque(s.x);
+    opaque(s.xm);
+    opaque(s.xp);
+}
+
 // ---------------------------------------------------------------- pairs
 
 template <typename T> struct Pair;
@@ -437,37 +456,23 @@ __device__ __forceinline__ void quad_set(uint2 &v, unsigned int b)
     w = (c & 1) ? ((w & 0x0000ffffu) | (b << 16)) : ((w & 0xffff0000u) | (b & 0xffffu));
 }
 
-// A/B pull step for 16-bit storage, four cells (x0 .. x0 + 3) per thread,
-// x0 a multiple of 4, nx a multiple of 4: every population is read and
-// written as one 8-byte quad, so the address work and the edge handling are
-// shared by four cells.  The quads are kept as raw 16-bit codes; the four
-// cells are collided one after another and their results written back into
-// the quads in place (ascending order: a +x population of cell c reads the
-// element c - 1, whose input is kept in `carry` before cell c - 1 overwrites
-// it).  Bitwise the same results as the one- and two-cell kernels.
-template <typename T, bool RHO0, bool WALLS>
-__global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Geo g, Relax<float> p)
+// Phase 1 of the four-cell steps: the 19 quads of the cells (x0 .. x0 + 3)
+// and, for the edge lanes, the element beyond the segment's edge (x0 - 1 for
+// +x populations, x0 + 4 for -x populations).  SWAP = false: A/B layout
+// (plane q at x - c_q; through a wall plane qbar of the own cell); SWAP =
+// true: AA odd layout (plane qbar at x - c_q; through a wall plane q).
+template <bool SWAP, bool WALLS, typename T>
+__device__ __forceinline__ void load4(const Planes<T> &P, const Site<WALLS> &s, const Geo &g, int lane, bool last,
+                                      bool active, uint2 (&quad)[Q], unsigned int (&e)[Q])
 {
-    const int lane = threadIdx.x & 31;
-    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (y >= g.ny) return;  // uniform across the warp
-    const bool active = x0 < g.nx;
-    const Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
     const int xs = s.x;
-    const bool last = lane == 31 || xs + 4 >= g.nx;
     const bool row_end = __any_sync(0xffffffffu, xs == 0 || xs + 4 >= g.nx);
-    // Phase 1: loads.  e: the element beyond the segment's edge (x0 - 1 for
-    // +x populations, x0 + 4 for -x populations), loaded by the edge lane.
-    uint2 quad[Q];
-    unsigned int e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q);
         const bool w = s.template wall_yz<-1>(q);
-        const unsigned short *srcq = reinterpret_cast<const unsigned short *>(src.p[q]);
-        const unsigned short *bncq = reinterpret_cast<const unsigned short *>(src.p[OPP(q)]);
+        const unsigned short *srcq = reinterpret_cast<const unsigned short *>(SWAP ? P.p[OPP(q)] : P.p[q]);
+        const unsigned short *bncq = reinterpret_cast<const unsigned short *>(SWAP ? P.p[q] : P.p[OPP(q)]);
         const int srow = s.template row_along<-1>(q);
         const unsigned short *ps = srcq + srow + xs;
         quad[q] = *reinterpret_cast<const uint2 *>(w ? bncq + s.own + xs : ps);
@@ -480,8 +485,14 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
             if (last && active && !w) e[q] = *a;
         }
     }
-    // Phase 2: neighbour elements across the lanes.
-    unsigned int carry[Q], right[Q];
+}
+
+// Phase 2: the neighbour elements across the lanes (all 32 lanes take part).
+// carry: the element before the quad (input of cell 0 of a +x population),
+// right: the element after it (input of cell 3 of a -x population).
+__device__ __forceinline__ void shuffle4(const uint2 (&quad)[Q], const unsigned int (&e)[Q], int lane, bool last,
+                                         unsigned int (&carry)[Q], unsigned int (&right)[Q])
+{
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q);
@@ -495,15 +506,23 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
             right[q] = last ? e[q] : r;
         }
     }
-    if (!active) return;
-    // Phase 3: four collisions, results written into the quads in place.
+}
+
+// Phase 3: four collisions, the results written into the quads in place
+// (ascending order: a +x population of cell c reads element c - 1, whose input
+// is kept in `carry` before cell c - 1 overwrites it).  SHIFTED = false (AA
+// even step): every input is the own element.
+template <typename T, bool RHO0, bool WALLS, bool SHIFTED>
+__device__ __forceinline__ void collide4(uint2 (&quad)[Q], unsigned int (&carry)[Q], const unsigned int (&right)[Q],
+                                         const Site<WALLS> &s, const Relax<float> &p)
+{
 #define LBM_AB4_CELL(c)                                                                      \
     {                                                                                        \
         float f[Q];                                                                          \
         _Pragma("unroll") for (int q = 0; q < Q; ++q)                                        \
         {                                                                                    \
-            const int cx = CX(q);                                                            \
-            const bool w = s.template wall_yz<-1>(q);                                        \
+            const int cx = SHIFTED ? CX(q) : 0;                                              \
+            const bool w = SHIFTED && s.template wall_yz<-1>(q);                             \
             unsigned int b;                                                                  \
             if (cx == 0 || w) b = quad_get<c>(quad[q]);                                      \
             else if (cx > 0) b = carry[q];                                                   \
@@ -513,15 +532,152 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
         collide_lean<float, RHO0>(f, p);                                                     \
         _Pragma("unroll") for (int q = 0; q < Q; ++q)                                        \
         {                                                                                    \
-            if (CX(q) > 0) carry[q] = quad_get<c>(quad[q]);                                   \
+            if (SHIFTED && CX(q) > 0) carry[q] = quad_get<c>(quad[q]);                        \
             quad_set<c>(quad[q], Bits16<T>::from_float(f[q]));                                \
         }                                                                                    \
     }
     LBM_AB4_CELL(0) LBM_AB4_CELL(1) LBM_AB4_CELL(2) LBM_AB4_CELL(3)
 #undef LBM_AB4_CELL
+}
+
+// A/B pull step for 16-bit storage, four cells (x0 .. x0 + 3) per thread,
+// x0 a multiple of 4, nx a multiple of 4: every population is read and
+// written as one 8-byte quad, so the address work and the edge handling are
+// shared by four cells.  The quads are kept as raw 16-bit codes and the four
+// results are written back into them.  Bitwise the same results as the one-
+// and two-cell kernels.
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Geo g, Relax<float> p)
+{
+    const int lane = threadIdx.x & 31;
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    const Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
+    const int xs = s.x;
+    const bool last = lane == 31 || xs + 4 >= g.nx;
+    uint2 quad[Q];
+    unsigned int e[Q], carry[Q], right[Q];
+    load4<false>(src, s, g, lane, last, active, quad, e);
+    shuffle4(quad, e, lane, last, carry, right);
+    if (!active) return;
+    collide4<T, RHO0, WALLS, true>(quad, carry, right, s, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
         *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(dst.p[q]) + s.own + xs) = quad[q];
+}
+
+// AA even step for 16-bit storage, four cells per thread: own quads of plane
+// q in, own quads of plane qbar out.  The in-place steps run four blocks per
+// SM (128 registers): at five the spills cost more than the occupancy gains
+// (0.77 against 0.84 of the copy bandwidth measured for the pair of steps).
+template <typename T, bool RHO0>
+__global__ void __launch_bounds__(128, 4) k_aa_even4(Planes<T> P, Geo g, Relax<float> p)
+{
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= g.nx || y >= g.ny) return;
+    const int own = (z * g.ny + y) * g.nx + x0;
+    uint2 quad[Q];
+    unsigned int carry[Q], right[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        quad[q] = *reinterpret_cast<const uint2 *>(reinterpret_cast<const unsigned short *>(P.p[q]) + own);
+        carry[q] = right[q] = 0u;  // unused: every input of the even step is the own element
+    }
+    const Site<false> s(x0, y, z, 4, g);
+    collide4<T, RHO0, false, false>(quad, carry, right, s, p);
+    int own_w = own;
+    opaque(own_w);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(P.p[OPP(q)]) + own_w) = quad[q];
+}
+
+// AA odd step for 16-bit storage, four cells per thread: gather plane qbar
+// from x - c_q (as k_ab4 with the planes swapped), collide, and write plane q
+// at x + c_q.  A +-x shifted write is assembled into the aligned quad
+// (x0 .. x0 + 3) of the target row from three own results and one of the
+// neighbouring lane (warp shuffle); at a segment's edge the lane writes the
+// three own elements of the aligned quad and the edge lane writes the fourth
+// result as a scalar into the neighbouring segment (or its periodic image, or
+// through an x wall into plane qbar of the own cell).  Through a y/z wall the
+// quad goes to plane qbar of the own cells.  Each location is written by one
+// thread, and read (for a value that is used) only by that thread, as in the
+// one-cell kernel.
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(128, 4) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p)
+{
+    const int lane = threadIdx.x & 31;
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform across the warp
+    const bool active = x0 < g.nx;
+    const Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
+    const int xs = s.x;
+    const bool last = lane == 31 || xs + 4 >= g.nx;
+    uint2 quad[Q];
+    unsigned int e[Q], carry[Q], right[Q];
+    load4<true>(P, s, g, lane, last, active, quad, e);
+    shuffle4(quad, e, lane, last, carry, right);
+    if (active) collide4<T, RHO0, WALLS, true>(quad, carry, right, s, p);
+    Site<WALLS> sw = s;
+    opaque(sw);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cx = CX(q);
+        const bool w = s.template wall_yz<1>(q);
+        unsigned short *dst = reinterpret_cast<unsigned short *>(P.p[q]);
+        unsigned short *bnc = reinterpret_cast<unsigned short *>(P.p[OPP(q)]);
+        const int trow = sw.template row_along<1>(q);
+        if (cx == 0) {
+            if (active) *reinterpret_cast<uint2 *>(w ? bnc + sw.own + sw.x : dst + trow + sw.x) = quad[q];
+        } else if (cx > 0) {
+            // target elements x0 .. x0 + 3 receive cells x0 - 1 .. x0 + 2
+            const unsigned int left = __shfl_up_sync(0xffffffffu, quad[q].y >> 16, 1);
+            if (!active) continue;
+            if (w) {
+                *reinterpret_cast<uint2 *>(bnc + sw.own + sw.x) = quad[q];
+                continue;
+            }
+            unsigned short *t = dst + trow + sw.x;
+            if (lane == 0) {  // element x0 belongs to the previous segment's last cell
+                t[1] = (unsigned short)(quad[q].x & 0xffffu);
+                *reinterpret_cast<unsigned int *>(t + 2) = __byte_perm(quad[q].x, quad[q].y, 0x5432);
+            } else {
+                uint2 v;
+                v.x = __byte_perm(left, quad[q].x, 0x5410);
+                v.y = __byte_perm(quad[q].x, quad[q].y, 0x5432);
+                *reinterpret_cast<uint2 *>(t) = v;
+            }
+            if (last)  // cell x0 + 3 goes to x0 + 4: the next segment, the periodic image, or a wall
+                *((WALLS && s.bxp) ? bnc + sw.own + sw.x + 3 : dst + trow + sw.xp) = (unsigned short)(quad[q].y >> 16);
+        } else {
+            // target elements x0 .. x0 + 3 receive cells x0 + 1 .. x0 + 4
+            const unsigned int rgt = __shfl_down_sync(0xffffffffu, quad[q].x & 0xffffu, 1);
+            if (!active) continue;
+            if (w) {
+                *reinterpret_cast<uint2 *>(bnc + sw.own + sw.x) = quad[q];
+                continue;
+            }
+            unsigned short *t = dst + trow + sw.x;
+            if (last) {  // element x0 + 3 belongs to the next segment's first cell
+                *reinterpret_cast<unsigned int *>(t) = __byte_perm(quad[q].x, quad[q].y, 0x5432);
+                t[2] = (unsigned short)(quad[q].y >> 16);
+            } else {
+                uint2 v;
+                v.x = __byte_perm(quad[q].x, quad[q].y, 0x5432);
+                v.y = __byte_perm(quad[q].y, rgt, 0x5432);
+                *reinterpret_cast<uint2 *>(t) = v;
+            }
+            if (lane == 0)  // cell x0 goes to x0 - 1: the previous segment, the periodic image, or a wall
+                *((WALLS && s.bxm) ? bnc + sw.own + sw.x : dst + trow + sw.xm) = (unsigned short)(quad[q].x & 0xffffu);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -545,7 +701,7 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
             k_aa_odd1<T, RHO0, WALLS, true><<<grid1, block, 0, stream>>>(D, g, p);
         return cudaGetLastError();
     }
-    const bool quads = sizeof(T) == 2 && kind == 0 && ls.cells_x == 4 && (g.nx % 4) == 0;
+    const bool quads = sizeof(T) == 2 && ls.cells_x == 4 && (g.nx % 4) == 0;
     const bool pairs = !quads && ls.cells_x >= 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
     if (quads) {
         // 128 threads; as many along x as one row needs (a multiple of 32), the rest along y
@@ -553,9 +709,13 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
         const dim3 block4(bx, 128 / bx, 1);
         const dim3 grid4((g.nx + 4 * bx - 1) / (4 * bx), (g.ny + block4.y - 1) / block4.y, g.nz);
         if constexpr (sizeof(T) == 2) {
-            const Planes<T> S = planes_of<T>(src, g.ncell);
             const Planes<T> D = planes_of<T>(dst, g.ncell);
-            k_ab4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(S, D, g, p);
+            if (kind == 0)
+                k_ab4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
+            else if (kind == 1)
+                k_aa_even4<T, RHO0><<<grid4, block4, 0, stream>>>(D, g, p);
+            else
+                k_aa_odd4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(D, g, p);
         }
         return cudaGetLastError();
     }

@@ -87,6 +87,24 @@ def test_aa_equals_ab_bitwise(nx, case, precision):
         assert torch.equal(ua, ub) and torch.equal(ra, rb)
 
 
+@pytest.mark.parametrize("precision", ["f16s", "bf16s"])
+@pytest.mark.parametrize("case", [0, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", [(3, 7, 4), (4, 9, 40), (3, 5, 388), (2, 3, 1040)])
+def test_aa_four_cells_is_bitwise(shape, case, precision):
+    """The four-cell AA steps (16-bit storage) against the one-cell A/B step,
+    bit for bit, after even and odd step counts: nx = 4 (a row is one quad,
+    its own periodic neighbour), a ragged warp (40), interior and row-end warps
+    (388), several blocks per row with a partial last block (1040); walls on
+    x (cases 4, 5), y (3) and z (4, 5) exercise the scalar edge writes
+    through a wall."""
+    kw = CASES[case]
+    rho, u = random_fields(shape, seed=13)
+    for steps in (1, 2, 5):
+        sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=1)
+        sb, _, _ = _run_gpu(shape, rho, u, steps, precision, "aa", kw, cells_x=4)
+        assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
+
+
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 def test_checkpoint_restore_is_bitwise(pattern):
     from paper_1803_04937_gb300.lbm import Simulation
