@@ -214,6 +214,18 @@ int lbm_moments(lbm_handle h, void *rho, void *u, int dtype);
 int lbm_reduce(lbm_handle h, double *out);
 
 /*
+ * Enstrophy of the current state into host *out: 1/2 <|curl u|^2>, the mean
+ * over all cells, with u from Eq. 17 and second-order central differences
+ * (u(x + e_a) - u(x - e_a)) / 2.  Periodic axes wrap; across a half-way
+ * bounce-back wall the ghost velocity is -u of the own cell.  FP64
+ * accumulation, deterministic for a given lattice size.  Needs a bound scratch
+ * buffer; synchronises the bound stream.  D3Q19 only.  Off the per-step path:
+ * each cell reads its six axis neighbours' populations.  Returns
+ * LBM_ENONFINITE if the result is not finite.
+ */
+int lbm_enstrophy(lbm_handle h, double *out);
+
+/*
  * lbm_reduce without a scratch buffer: the same FP64 reductions of the
  * current state into host out[LBM_RED_COUNT], for callers that cannot
  * allocate device memory (for example a host application that hands the

@@ -48,6 +48,7 @@ _SIGS = {
     "lbm_step": (_i, [_vp, _i]),
     "lbm_moments": (_i, [_vp, _vp, _vp, _i]),
     "lbm_reduce": (_i, [_vp, ctypes.POINTER(_d)]),
+    "lbm_enstrophy": (_i, [_vp, ctypes.POINTER(_d)]),
     "lbm_reduce_noalloc": (_i, [_vp, ctypes.POINTER(_d)]),
     "lbm_steps_done": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_get_pdfs": (_i, [_vp, _vp]),

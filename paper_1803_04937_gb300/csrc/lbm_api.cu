@@ -429,6 +429,26 @@ int lbm_reduce(lbm_handle h, double *out)
     return LBM_OK;
 }
 
+int lbm_enstrophy(lbm_handle h, double *out)
+{
+    int s = check_ready(h);
+    if (s) return s;
+    if ((s = d3q19_only(h, "lbm_enstrophy"))) return s;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (!h->scratch) return fail(h, LBM_ESTATE, "lbm_enstrophy needs a scratch buffer (lbm_bind)");
+    if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
+    double *result = h->scratch + (size_t)lbm::reduce_blocks() * 8;
+    cudaError_t e = lbm::launch_enstrophy(h->precision, layout(h), current(h), h->scratch, result, geo(h), coll(h),
+                                          h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_enstrophy");
+    e = cudaMemcpyAsync(out, result, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_enstrophy copy");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_enstrophy sync");
+    if (!std::isfinite(*out)) return fail(h, LBM_ENONFINITE, "enstrophy is not finite");
+    return LBM_OK;
+}
+
 int lbm_reduce_noalloc(lbm_handle h, double *out)
 {
     int s = check_ready(h);

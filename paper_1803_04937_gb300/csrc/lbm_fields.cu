@@ -174,6 +174,81 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *part
     if (threadIdx.x == 0) result[7] = 0.0;
 }
 
+// Enstrophy 1/2 <|curl u|^2> of the state, with second-order central
+// differences of u (Eq. 17) between the axis neighbours.  Periodic axes wrap;
+// across a half-way bounce-back wall the ghost velocity is -u of the own cell
+// (the wall at rest halfway between them).  Each cell gathers its six
+// neighbours' populations (off the per-step path; the neighbours' rows are
+// shared through L1/L2).  Deterministic: fixed grid, fixed per-thread order,
+// fixed trees.
+template <typename T, int L>
+__device__ __forceinline__ void velocity_at(const T *__restrict__ grid, int x, int y, int z, const Geo &g,
+                                            const Coll<typename Storage<T>::R> &p, double u[3])
+{
+    using R = typename Storage<T>::R;
+    const Cell c(x, y, z, g);
+    R f[Q];
+    gather<L>(grid, c, g.ncell, f);
+    R drho, rho0, uv[3];
+    macro(f, p, drho, rho0, uv);
+    u[0] = uv[0];
+    u[1] = uv[1];
+    u[2] = uv[2];
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(RED_THREADS) k_enstrophy(const T *__restrict__ grid, double *partial, Geo g,
+                                                           Coll<typename Storage<T>::R> p)
+{
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const long long nxy = (long long)g.nx * g.ny;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const bool wall[3] = {g.wall_x != 0, g.wall_y != 0, g.wall_z != 0};
+    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(cell / nxy);
+        const int rem = (int)(cell - z * nxy);
+        const int y = rem / g.nx;
+        const int x = rem - y * g.nx;
+        const int pos[3] = {x, y, z};
+        double own[3];
+        velocity_at<T, L>(grid, x, y, z, g, p, own);
+        // D[a][i] = (u_i(x + e_a) - u_i(x - e_a)) / 2
+        double D[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double up[3], um[3];
+            int qp[3] = {x, y, z}, qm[3] = {x, y, z};
+            const bool wp = wall[a] && pos[a] == n[a] - 1, wm = wall[a] && pos[a] == 0;
+            qp[a] = pos[a] == n[a] - 1 ? 0 : pos[a] + 1;
+            qm[a] = pos[a] == 0 ? n[a] - 1 : pos[a] - 1;
+            if (wp) { up[0] = -own[0]; up[1] = -own[1]; up[2] = -own[2]; }
+            else velocity_at<T, L>(grid, qp[0], qp[1], qp[2], g, p, up);
+            if (wm) { um[0] = -own[0]; um[1] = -own[1]; um[2] = -own[2]; }
+            else velocity_at<T, L>(grid, qm[0], qm[1], qm[2], g, p, um);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) D[a][i] = 0.5 * (up[i] - um[i]);
+        }
+        const double wx = D[1][2] - D[2][1];
+        const double wy = D[2][0] - D[0][2];
+        const double wz = D[0][1] - D[1][0];
+        acc += wx * wx + wy * wy + wz * wz;
+    }
+    const double v = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x * 8] = v;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_enstrophy_final(const double *partial, int nblocks,
+                                                                 double *result, double ncell)
+{
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[b * 8];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) result[0] = 0.5 * v / ncell;
+}
+
 // ---------------------------------------------------------------- dispatch
 
 template <typename F>
@@ -287,6 +362,24 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static double *g_reduce_scratch_dev[NOALLOC_MAX_DEVICES];
 
 int reduce_noalloc_capacity_doubles() { return NOALLOC_DOUBLES; }
+
+cudaError_t launch_enstrophy(int prec, int layout, const void *grid, double *scratch, double *result, const Geo &g,
+                             const CollBoth &c, cudaStream_t s)
+{
+    cudaError_t e = by_prec(prec, [&](auto tag) {
+        using T = decltype(tag);
+        using R = typename Storage<T>::R;
+        const Coll<R> p = to_coll<R>(c);
+        const T *gr = static_cast<const T *>(grid);
+        if (layout == AB) k_enstrophy<T, AB><<<RED_BLOCKS, RED_THREADS, 0, s>>>(gr, scratch, g, p);
+        else if (layout == AA_EVEN) k_enstrophy<T, AA_EVEN><<<RED_BLOCKS, RED_THREADS, 0, s>>>(gr, scratch, g, p);
+        else k_enstrophy<T, AA_ODD><<<RED_BLOCKS, RED_THREADS, 0, s>>>(gr, scratch, g, p);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    k_enstrophy_final<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, result, (double)g.ncell);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_reduce_noalloc(int prec, int layout, const void *grid, const Geo &g, const CollBoth &c,
                                   cudaStream_t s, double **result)

@@ -50,6 +50,10 @@ int reduce_blocks();
 cudaError_t launch_reduce(int prec, int layout, const void *grid, double *scratch, double *scratch_result,
                           const Geo &g, const CollBoth &c, cudaStream_t stream);
 
+// Enstrophy 1/2 <|curl u|^2> (central differences) of the state into result[0].
+cudaError_t launch_enstrophy(int prec, int layout, const void *grid, double *scratch, double *result,
+                             const Geo &g, const CollBoth &c, cudaStream_t stream);
+
 // The same reduction with its scratch in a static device array (lbm_reduce_noalloc);
 // *result receives the device address of the LBM_RED_COUNT results.
 int reduce_noalloc_capacity_doubles();

@@ -158,6 +158,12 @@ class Simulation:
         return {"mass": out[0], "energy": out[1], "momentum": (out[2], out[3], out[4]), "umax": out[5],
                 "nonfinite": int(out[6]), "status": s}
 
+    def enstrophy(self):
+        """FP64 enstrophy 1/2 <|curl u|^2> of the current state (central differences; synchronises)."""
+        out = ctypes.c_double()
+        check(self._lib.lbm_enstrophy(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
     def steps_done(self):
         t = ctypes.c_longlong()
         check(self._lib.lbm_steps_done(self._h, ctypes.byref(t)), self._h)

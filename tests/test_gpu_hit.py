@@ -16,17 +16,6 @@ from tests._helpers import oracle_config, rel_maxnorm
 pytestmark = pytest.mark.gpu
 
 
-def _enstrophy(u):
-    """1/2 <|curl u|^2> with second-order central differences (periodic)."""
-    def d(f, axis):
-        return 0.5 * (torch.roll(f, -1, axis) - torch.roll(f, 1, axis))
-    ux, uy, uz = u[0], u[1], u[2]  # arrays [z, y, x]
-    wx = d(uz, 1) - d(uy, 0)
-    wy = d(ux, 0) - d(uz, 2)
-    wz = d(uy, 2) - d(ux, 1)
-    return 0.5 * float((wx.double() ** 2 + wy.double() ** 2 + wz.double() ** 2).mean())
-
-
 def _series(n, precision, equilibrium, steps, every, pattern="aa"):
     from paper_1803_04937_gb300.lbm import Simulation
     sim = Simulation(n, n, n, equilibrium=equilibrium, collision="srt", tau=0.51, precision=precision,
@@ -35,7 +24,6 @@ def _series(n, precision, equilibrium, steps, every, pattern="aa"):
     sim.init(None, u if precision == "f64" else u.float())
     del rho, u
     E, Z = [], []
-    dt = torch.float64 if precision == "f64" else torch.float32
     for t in range(0, steps + 1, every):
         if t:
             sim.step(every)
@@ -44,10 +32,8 @@ def _series(n, precision, equilibrium, steps, every, pattern="aa"):
             E.append(float("nan"))
             Z.append(float("nan"))
             break
-        _, u = sim.moments(dt)
         E.append(red["energy"] / sim.ncell)
-        Z.append(_enstrophy(u))
-        del u
+        Z.append(sim.enstrophy())
     sim.close()
     return np.array(E), np.array(Z)
 
