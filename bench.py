@@ -307,7 +307,7 @@ def e2e(args, n, calls=3, steps_per_call=100):
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(target_seconds, cross=32):
+def oracle_sample(target_seconds, cross=32, single_thread_seconds=0.0):
     """Times the FP64 CPU oracle on a 256 x c x c periodic slab of the shear-wave
     workload (the flow is invariant in y and z, so every slab is an exact
     sample of the 256^3 lattice), sized to about `target_seconds`."""
@@ -330,9 +330,26 @@ def oracle_sample(target_seconds, cross=32):
     f = oracle.step(cfg, f, steps)
     t = time.perf_counter() - t0
     assert np.isfinite(f).all()
-    return {"value": cfg.ncell * steps / t / 1e6, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "FP64 C oracle, %d steps of a periodic 256x%dx%d slab of the shear-wave workload "
-                      "(y,z-invariant, so an exact sample of 256^3), %.1f s" % (steps, c, c, t)}
+    out = {"value": cfg.ncell * steps / t / 1e6, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": "FP64 C oracle, %d steps of a periodic 256x%dx%d slab of the shear-wave workload "
+                     "(y,z-invariant, so an exact sample of 256^3), %.1f s" % (steps, c, c, t)}
+    if single_thread_seconds > 0:
+        # the same oracle on one thread, on a slab sized to about single_thread_seconds
+        cfg.nthreads = 1
+        f = oracle.init(cfg, rho.numpy(), u.numpy())
+        t0 = time.perf_counter()
+        oracle.step(cfg, f, 1)
+        t1 = time.perf_counter() - t0
+        steps1 = max(1, int(single_thread_seconds / max(t1, 1e-6)))
+        t0 = time.perf_counter()
+        oracle.step(cfg, f, steps1)
+        t1 = time.perf_counter() - t0
+        out["value_1_thread"] = cfg.ncell * steps1 / t1 / 1e6
+        out["sample_1_thread"] = "%d steps of the same slab on 1 thread, %.1f s" % (steps1, t1)
+        # the thread count is process-wide in OpenMP: restore it
+        tiny = oracle.Config(1, 1, 1, nthreads=out["cores"])
+        oracle.step(tiny, oracle.init(tiny, np.ones((1, 1, 1)), np.zeros((3, 1, 1, 1))), 1)
+    return out
 
 
 def run_reference(args):
@@ -457,7 +474,7 @@ def run_native(args):
     elif rank == 0:
         line["e2e"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(12.0)
+        line["cpu_baseline"] = oracle_sample(12.0, single_thread_seconds=4.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
