@@ -50,6 +50,8 @@ def parse_args(argv=None):
     p.add_argument("--block", type=str, default=None, help="step kernel block 'bx,by'")
     p.add_argument("--cells-x", type=int, choices=[1, 2, 4], default=None,
                    help="step kernel cells per thread along x (default: library's choice)")
+    p.add_argument("--graphs", type=int, choices=[0, 1], default=None,
+                   help="1: lbm_step replays 16-step CUDA graphs (library default); 0: one launch per step")
     p.add_argument("--only-adjoint", action="store_true",
                    help="time only the adjoint workload (128^3) and print its figures")
     p.add_argument("--no-extras", action="store_true", help="main line only (profiling runs)")
@@ -179,12 +181,24 @@ def shear_workload(nx, ny, nz, device):
 
 # ------------------------------------------------------------------ GPU timing
 
+GRAPH_STEPS = 16  # lbm_step replays CUDA graphs of this many steps
+
+
+def warm(sim, warmup):
+    """`warmup` untimed steps, then GRAPH_STEPS more so that the CUDA graph for
+    the grid (A/B) or parity (AA) the timed steps start from is captured
+    before the timed region (an even count returns to the same grid)."""
+    sim.step(warmup)
+    sim.step(GRAPH_STEPS)
+    return warmup + GRAPH_STEPS
+
+
 def time_steps(sim, steps, warmup):
     """Average device time (s) per lattice step over `steps` launches, after
     `warmup` launches; CUDA events on the simulation's stream."""
     import torch
     s = sim.stream
-    sim.step(warmup)
+    warm(sim, warmup)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -200,7 +214,8 @@ def make_sim(args, n, precision=None, pattern=None, collision=None, equilibrium=
     block = tuple(int(x) for x in args.block.split(",")) if args.block else None
     sim = Simulation(n, n, n, equilibrium=equilibrium or args.equilibrium, collision=collision or args.collision,
                      tau=args.tau, precision=precision or args.precision, pattern=pattern or args.pattern,
-                     device=device, block=block, cells_x=args.cells_x, stencil=stencil)
+                     device=device, block=block, cells_x=args.cells_x, stencil=stencil,
+                     graphs=None if args.graphs is None else bool(args.graphs))
     rho, u = shear_workload(n, n, n, device)
     sim.init(rho, u.float() if (precision or args.precision) != "f64" else u)
     del rho, u
@@ -291,7 +306,7 @@ def e2e(args, n, calls=3, steps_per_call=100):
     rho_h = rho.to(dt).pin_memory()
     u_h = u.to(dt).pin_memory()
     out = (torch.empty(rho_h.shape, dtype=dt, pin_memory=True), torch.empty(u_h.shape, dtype=dt, pin_memory=True))
-    sim.run_host(rho_h, u_h, 5, out)  # warm-up
+    sim.run_host(rho_h, u_h, steps_per_call, out)  # warm-up (also captures the step graph)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(calls):
@@ -397,7 +412,7 @@ def run_native(args):
     device = torch.device("cuda", local)
     n = args.n
     sim = make_sim(args, n, device=device)
-    sim.step(args.warmup)
+    warmup_run = warm(sim, args.warmup)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -439,6 +454,7 @@ def run_native(args):
         "vs_baseline": None, "dtype": DTYPE_NAME[args.precision], "data": "synthetic",
         "config": {"workload": "D3Q19 shear wave u_y=0.01 sin(2 pi x/%d) on U_x=0.1, periodic %d^3" % (n, n),
                    "equilibrium": args.equilibrium, "collision": args.collision, "tau": args.tau,
+                   "warmup_steps_run": warmup_run,
                    "precision": args.precision, "pattern": args.pattern,
                    "l2": "inputs larger than L2 (%.2f GB per grid vs 129 MB L2)" % (
                        BYTES_PER_LUP[args.precision] / 2 * cells / 1e9),

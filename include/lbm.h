@@ -115,6 +115,11 @@ typedef struct lbm_ctx *lbm_handle;
                                      (bulk viscosity (2/9)(1/omega - 1/2)); 0 < v < 2, default 1 */
 #define LBM_OPT_MRT_OMEGA_4    17 /* LBM_MRT: rate of the fourth-order moments; 0 < v < 2,
                                      default 1 */
+#define LBM_OPT_GRAPHS    18  /* 1 (default): lbm_step replays captured CUDA graphs of 16 steps
+                                 (built on first use from the current grid or parity, dropped
+                                 by lbm_set_option and lbm_bind; not used while the bound stream
+                                 is being captured by the caller); 0: one launch per step.
+                                 Same results either way. */
 
 /* lbm_reduce output slots */
 #define LBM_RED_MASS      0   /* sum_x rho */

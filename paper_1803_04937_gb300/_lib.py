@@ -22,7 +22,7 @@ OPT_TRT_MAGIC, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = 1, 2, 3, 4
 OPT_WALLS_X, OPT_WALLS_Y, OPT_WALLS_Z = 5, 6, 7
 OPT_RHO0_MODE, OPT_PATTERN, OPT_TAU, OPT_EQUILIBRIUM, OPT_COLLISION = 8, 9, 10, 11, 12
 OPT_BLOCK_X, OPT_BLOCK_Y, OPT_CELLS_X = 13, 14, 15
-OPT_MRT_OMEGA_BULK, OPT_MRT_OMEGA_4 = 16, 17
+OPT_MRT_OMEGA_BULK, OPT_MRT_OMEGA_4, OPT_GRAPHS = 16, 17, 18
 RED_MASS, RED_ENERGY, RED_JX, RED_JY, RED_JZ, RED_UMAX, RED_NONFINITE = range(7)
 RED_COUNT = 8
 

@@ -21,6 +21,7 @@
 //     dL/domega- = -sum_q mu-_q (f_q - feq_q) - 1/2 sum_q mu_q F_q.
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
+#include "lbm_step.cuh"  // Planes, Site, gather1 (the A/B pull of the forward step)
 
 namespace lbm {
 
@@ -128,10 +129,13 @@ __device__ __forceinline__ void adj_pair(const CellEq<R, false> &e, const R mu[Q
     cf += D * fraw[k];
 }
 
-template <typename T, typename L>
-__global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 : 4) k_adjoint_step(const T *__restrict__ state, const L *__restrict__ lam_next,
-                                                      L *__restrict__ lam, double *partial, Geo g,
-                                                      AdjConst<typename Storage<T>::R> p)
+// Addressing as in the forward step kernels: plane base pointers from the
+// kernel parameters, nine wrapped row offsets per thread (Site), and no
+// bounce-back logic when the lattice is periodic (WALLS = false).
+template <typename T, typename L, bool WALLS>
+__global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 : 4)
+    k_adjoint_step(Planes<T> state, Planes<L> lam_next, Planes<L> lam, double *partial, Geo g,
+                   AdjConst<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     __shared__ typename Storage<T>::R shp[256], shm[256];  // compute precision
@@ -140,19 +144,24 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
     const int z = blockIdx.z;
     R gp_cell = R(0), gm_cell = R(0);  // this cell's terms of dL/domega+ and dL/domega-
     if (x < g.nx && y < g.ny) {
-        Cell c(x, y, z, g);
-        const int self = c.self();
+        const Site<WALLS> st(x, y, z, 1, g);
+        const int self = st.own + x;
         // forward populations of the cell at time t (rho0 = 1), and S^T: the
         // value that left x along c_q arrived at x + c_q (or, through a wall,
         // at the opposite slot of x).  All 38 loads are issued first.
         R f[Q], mu[Q];
-        gather<AB>(state, c, g.ncell, f);
+        gather1<false>(state, st, f);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            bool wall;
-            int dst = c.template along<1>(q, wall);
-            long long off = wall ? (long long)OPP(q) * g.ncell + self : (long long)q * g.ncell + dst;
-            mu[q] = R(lam_next[off]);
+            const int cx = CX(q);
+            const int xt = cx == 0 ? x : (cx > 0 ? st.xp : st.xm);
+            bool w = st.template wall_yz<1>(q);
+            if (WALLS) {
+                if (cx > 0) w |= st.bxp;
+                if (cx < 0) w |= st.bxm;
+            }
+            const L *a = w ? lam_next.p[OPP(q)] + self : lam_next.p[q] + st.template row_along<1>(q) + xt;
+            mu[q] = R(*a);
         }
         const CellEq<R, false> e(f, p.r);
         // omega gradients of this cell:
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             const R gd = wp * (mu[0] * (R(1) / R(3)) - (fs - face[i]) * (R(1) / R(6)) + edge[i] * (R(1) / R(12)));
             G[i] = gs + p.kappa * gd * u[i];
         }
-        lam[self] = L((R(1) - wp) * mu[0] + A);
+        lam.p[0][self] = L((R(1) - wp) * mu[0] + A);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int q = 2 * k + 1;
@@ -219,8 +228,8 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             const R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
             const R t = A - p.r.hp * S;
             const R hd = p.r.hm * D;
-            lam[(long long)q * g.ncell + self] = L(mu[q] + t - hd + cg);
-            lam[(long long)(q + 1) * g.ncell + self] = L(mu[q + 1] + t + hd - cg);
+            lam.p[q][self] = L(mu[q] + t - hd + cg);
+            lam.p[q + 1][self] = L(mu[q + 1] + t + hd - cg);
         }
     }
     // Block partial in FP64: the per-cell terms are staged in shared memory (in
@@ -302,8 +311,13 @@ static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam
 {
     using R = typename Storage<T>::R;
     AdjConst<R> p = to_adj<R>(cb);
-    k_adjoint_step<T, L><<<adj_grid(g), adj_block(), 0, s>>>((const T *)state, (const L *)lam_next, (L *)lam,
-                                                              scratch, g, p);
+    const Planes<T> S = planes_of<T>(const_cast<void *>(state), g.ncell);
+    const Planes<L> Ln = planes_of<L>(const_cast<void *>(lam_next), g.ncell);
+    const Planes<L> Lo = planes_of<L>(lam, g.ncell);
+    if (g.wall_x || g.wall_y || g.wall_z)
+        k_adjoint_step<T, L, true><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, scratch, g, p);
+    else
+        k_adjoint_step<T, L, false><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, scratch, g, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adjoint_final<<<1, 256, 0, s>>>(scratch, (long long)adjoint_blocks(g), grad_omega);

@@ -25,6 +25,8 @@ struct lbm_ctx {
     int pattern = LBM_PATTERN_AB;
     int bx = 128, by = 2;
     int cells_x = 1;
+    int graphs = 1;                                // replay GRAPH_STEPS-step CUDA graphs in lbm_step
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // by starting A/B grid or AA parity
     void *a = nullptr, *b = nullptr;
     double *scratch = nullptr;
     cudaStream_t stream = nullptr;
@@ -145,6 +147,62 @@ int check_dtype(lbm_handle h, int dtype)
     return LBM_OK;
 }
 
+// One time step on stream st from the A/B grid `cur` or AA parity `parity`,
+// which are advanced on success.
+cudaError_t launch_one(const lbm_ctx *h, cudaStream_t st, int &cur, int &parity, const lbm::Geo &g,
+                       const lbm::CollBoth &c, const lbm::LaunchShape &shape)
+{
+    cudaError_t e;
+    if (h->pattern == LBM_PATTERN_AB) {
+        void *src = cur ? h->b : h->a;
+        void *dst = cur ? h->a : h->b;
+        e = h->stencil == LBM_D3Q27 ? lbm::launch_step27(h->precision, src, dst, g, c, shape, st)
+                                    : lbm::launch_step(h->precision, 0, src, dst, g, c, shape, st);
+        if (e == cudaSuccess) cur ^= 1;
+    } else {
+        e = lbm::launch_step(h->precision, parity ? 2 : 1, h->a, h->a, g, c, shape, st);
+        if (e == cudaSuccess) parity ^= 1;
+    }
+    return e;
+}
+
+// Steps per CUDA graph: even, so that a replay returns to the grid (A/B) or
+// parity (AA) it started from.
+constexpr int GRAPH_STEPS = 16;
+
+void drop_graphs(lbm_ctx *h)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+        h->gexec[i] = nullptr;
+    }
+}
+
+// Captures GRAPH_STEPS steps starting from `slot` (A/B grid or AA parity) on
+// a private stream (thread-local capture mode, so other threads' work is not
+// affected) and instantiates them.
+cudaError_t build_graph(lbm_ctx *h, int slot, const lbm::Geo &g, const lbm::CollBoth &c,
+                        const lbm::LaunchShape &shape)
+{
+    cudaStream_t ps = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int cur = slot, parity = slot;
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < GRAPH_STEPS && le == cudaSuccess; ++k) le = launch_one(h, ps, cur, parity, g, c, shape);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(ps, &graph);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[slot], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    cudaStreamDestroy(ps);
+    if (e != cudaSuccess) h->gexec[slot] = nullptr;
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -226,6 +284,7 @@ int lbm_create(int nx, int ny, int nz, int stencil, int equilibrium, int collisi
 int lbm_destroy(lbm_handle h)
 {
     if (!h) return LBM_EINVAL;
+    drop_graphs(h);
     delete h;
     return LBM_OK;
 }
@@ -234,6 +293,7 @@ int lbm_set_option(lbm_handle h, int key, double v)
 {
     if (!h) return LBM_EINVAL;
     if (!std::isfinite(v)) return fail(h, LBM_EINVAL, "option value must be finite");
+    drop_graphs(h);  // captured kernels carry the old parameters
     switch (key) {
     case LBM_OPT_TRT_MAGIC:
         if (!(v > 0)) return fail(h, LBM_EINVAL, "TRT magic parameter must be > 0");
@@ -281,6 +341,10 @@ int lbm_set_option(lbm_handle h, int key, double v)
         if (!(v > 0.0 && v < 2.0)) return fail(h, LBM_EINVAL, "MRT rates must lie in (0, 2)");
         (key == LBM_OPT_MRT_OMEGA_BULK ? h->omega_bulk : h->omega_4) = v;
         return LBM_OK;
+    case LBM_OPT_GRAPHS:
+        if (v != 0.0 && v != 1.0) return fail(h, LBM_EINVAL, "graphs option must be 0 or 1");
+        h->graphs = (int)v;
+        return LBM_OK;
     case LBM_OPT_CELLS_X:
         if (v != 1.0 && v != 2.0 && v != 4.0) return fail(h, LBM_EINVAL, "cells per thread must be 1, 2 or 4");
         h->cells_x = (int)v;
@@ -318,6 +382,7 @@ int lbm_get_option(lbm_handle h, int key, double *v)
     case LBM_OPT_MRT_OMEGA_BULK: *v = h->omega_bulk; return LBM_OK;
     case LBM_OPT_MRT_OMEGA_4: *v = h->omega_4; return LBM_OK;
     case LBM_OPT_CELLS_X: *v = h->cells_x; return LBM_OK;
+    case LBM_OPT_GRAPHS: *v = h->graphs; return LBM_OK;
     case LBM_OPT_BLOCK_X: *v = h->bx; return LBM_OK;
     case LBM_OPT_BLOCK_Y: *v = h->by; return LBM_OK;
     }
@@ -341,6 +406,7 @@ int lbm_bind(lbm_handle h, void *pdf_a, void *pdf_b, void *scratch, void *stream
     if (h->pattern == LBM_PATTERN_AB && pdf_a == pdf_b) return fail(h, LBM_EINVAL, "pdf_a and pdf_b must differ");
     if (!aligned(pdf_a) || (pdf_b && !aligned(pdf_b)) || (scratch && !aligned(scratch)))
         return fail(h, LBM_EINVAL, "device buffers must be 256-byte aligned");
+    drop_graphs(h);  // captured kernels carry the old grid pointers
     h->a = pdf_a;
     h->b = h->pattern == LBM_PATTERN_AB ? pdf_b : nullptr;
     h->scratch = (double *)scratch;
@@ -376,18 +442,29 @@ int lbm_step(lbm_handle h, int n)
     const lbm::Geo g = geo(h);
     const lbm::CollBoth c = coll(h);
     const lbm::LaunchShape shape{h->bx, h->by, h->cells_x};
-    for (int i = 0; i < n; ++i) {
-        cudaError_t e;
-        if (h->pattern == LBM_PATTERN_AB) {
-            void *src = current(h);
-            void *dst = h->cur ? h->a : h->b;
-            e = h->stencil == LBM_D3Q27 ? lbm::launch_step27(h->precision, src, dst, g, c, shape, h->stream)
-                                        : lbm::launch_step(h->precision, 0, src, dst, g, c, shape, h->stream);
-            if (e == cudaSuccess) h->cur ^= 1;
-        } else {
-            e = lbm::launch_step(h->precision, h->parity ? 2 : 1, h->a, h->a, g, c, shape, h->stream);
-            if (e == cudaSuccess) h->parity ^= 1;
+    int i = 0;
+    if (h->graphs && n >= GRAPH_STEPS) {
+        // Replay whole graphs of GRAPH_STEPS steps (one launch call for many
+        // kernels), unless the caller is capturing the bound stream itself:
+        // then the plain launches below are recorded into the caller's graph.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(h->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            const int slot = h->pattern == LBM_PATTERN_AB ? h->cur : h->parity;
+            if (!h->gexec[slot] && build_graph(h, slot, g, c, shape) != cudaSuccess) {
+                cudaGetLastError();  // capture failed: step without graphs
+                h->graphs = 0;
+            }
+            if (h->gexec[slot]) {
+                for (; i + GRAPH_STEPS <= n; i += GRAPH_STEPS) {
+                    cudaError_t e = cudaGraphLaunch(h->gexec[slot], h->stream);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step (graph)");
+                    h->t += GRAPH_STEPS;
+                }
+            }
         }
+    }
+    for (; i < n; ++i) {
+        cudaError_t e = launch_one(h, h->stream, h->cur, h->parity, g, c, shape);
         if (e != cudaSuccess) return cuda_fail(h, e, "lbm_step");
         ++h->t;
     }

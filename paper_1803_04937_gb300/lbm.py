@@ -60,7 +60,7 @@ class Simulation:
     def __init__(self, nx, ny, nz, equilibrium="improved", collision="srt", tau=0.8, precision="f32",
                  trt_magic=3.0 / 16.0, force=(0.0, 0.0, 0.0), walls=(False, False, False), rho0_is_rho=False,
                  pattern="ab", device="cuda", stream=None, block=None, cells_x=None, stencil=19, omega_bulk=1.0,
-                 omega_4=1.0):
+                 omega_4=1.0, graphs=None):
         self._lib = lib = _lib.load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.device = torch.device(device)
@@ -88,6 +88,8 @@ class Simulation:
             self._set(_lib.OPT_BLOCK_Y, block[1])
         if cells_x is not None:
             self._set(_lib.OPT_CELLS_X, cells_x)
+        if graphs is not None:
+            self._set(_lib.OPT_GRAPHS, 1.0 if graphs else 0.0)
         self.pattern = pattern
         pdf_bytes = ctypes.c_size_t()
         ngrids = ctypes.c_int()

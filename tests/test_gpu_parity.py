@@ -105,6 +105,43 @@ def test_aa_four_cells_is_bitwise(shape, case, precision):
         assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
 
 
+@pytest.mark.parametrize("stencil,pattern,precision", [(19, "ab", "f32"), (19, "aa", "f32"), (19, "ab", "f16s"),
+                                                       (19, "aa", "bf16s"), (27, "ab", "f32"), (19, "ab", "f64")])
+def test_graph_replay_is_bitwise(stencil, pattern, precision):
+    """lbm_step replays captured 16-step CUDA graphs for long step counts; the
+    results equal one launch per step bit for bit, across odd remainders,
+    option changes (the graphs are rebuilt with the new parameters) and a
+    checkpoint restore."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    shape = (6, 10, 40)
+    rho, u = random_fields(shape, seed=31)
+    kw = dict(stencil=stencil, pattern=pattern, precision=precision, collision="trt", tau=0.7,
+              walls=(False, True, False), force=(1e-4, 0, 0),
+              equilibrium="standard" if stencil == 27 else "improved")
+    sims = []
+    for graphs in (True, False):
+        sim = Simulation(40, 10, 6, graphs=graphs, **kw)
+        sim.init(rho.cuda(), u.cuda() if precision == "f64" else u.float().cuda())
+        sim.step(37)
+        sim._set(_lib_opt("OPT_TAU"), 0.9)
+        sim.step(16)
+        sim.step(3)
+        sim.step(33)
+        sims.append(sim)
+    assert torch.equal(sims[0].get_pdfs(), sims[1].get_pdfs())
+    assert sims[0].steps_done() == sims[1].steps_done() == 89
+    ck = sims[0].get_pdfs()
+    sims[0].set_pdfs(ck)
+    sims[0].step(20)
+    sims[1].step(20)
+    assert torch.equal(sims[0].get_pdfs(), sims[1].get_pdfs())
+
+
+def _lib_opt(name):
+    from paper_1803_04937_gb300 import _lib
+    return getattr(_lib, name)
+
+
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 def test_checkpoint_restore_is_bitwise(pattern):
     from paper_1803_04937_gb300.lbm import Simulation
