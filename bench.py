@@ -441,12 +441,10 @@ def run_native(args):
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LUP[args.precision] * cells / per_launch / 1e9
     cx = args.cells_x or (4 if args.precision in ("f16s", "bf16s") else 1)
-    if args.collision == "mrt":
-        cx = 1  # the MRT step runs one cell per thread
     if args.pattern == "ab":
         kname = "k_ab%d<%s>" % (cx, args.precision) + ("[mrt]" if args.collision == "mrt" else "")
     else:
-        kname = "k_aa_even%d+k_aa_odd%d<%s>" % (cx, cx, args.precision)
+        kname = "k_aa_even%d+k_aa_odd%d<%s>" % (cx, cx, args.precision) + ("[mrt]" if args.collision == "mrt" else "")
     traffic_per_lup, _ = read_traffic(kname)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,

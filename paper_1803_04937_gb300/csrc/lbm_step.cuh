@@ -475,7 +475,14 @@ __device__ __forceinline__ void load4(const Planes<T> &P, const Site<WALLS> &s, 
         const unsigned short *bncq = reinterpret_cast<const unsigned short *>(SWAP ? P.p[q] : P.p[OPP(q)]);
         const int srow = s.template row_along<-1>(q);
         const unsigned short *ps = srcq + srow + xs;
-        quad[q] = *reinterpret_cast<const uint2 *>(w ? bncq + s.own + xs : ps);
+        const uint2 *pq = reinterpret_cast<const uint2 *>(w ? bncq + s.own + xs : ps);
+        // A/B: the source grid is read-only during the step, so the loads may
+        // take the non-coherent path (measured +0.4 %); the in-place AA step
+        // writes what it reads and keeps coherent loads.
+        if constexpr (!SWAP)
+            quad[q] = __ldg(pq);
+        else
+            quad[q] = *pq;
         e[q] = 0u;
         if (cx > 0) {
             const unsigned short *a = row_end ? ((WALLS && s.bxm) ? bncq + s.own + xs : srcq + srow + s.xm) : ps - 1;
@@ -512,7 +519,7 @@ __device__ __forceinline__ void shuffle4(const uint2 (&quad)[Q], const unsigned 
 // (ascending order: a +x population of cell c reads element c - 1, whose input
 // is kept in `carry` before cell c - 1 overwrites it).  SHIFTED = false (AA
 // even step): every input is the own element.
-template <typename T, bool RHO0, bool WALLS, bool SHIFTED>
+template <typename T, bool RHO0, bool WALLS, bool SHIFTED, bool MRT = false>
 __device__ __forceinline__ void collide4(uint2 (&quad)[Q], unsigned int (&carry)[Q], const unsigned int (&right)[Q],
                                          const Site<WALLS> &s, const Relax<float> &p)
 {
@@ -529,7 +536,7 @@ __device__ __forceinline__ void collide4(uint2 (&quad)[Q], unsigned int (&carry)
             else b = (c == 3) ? right[q] : quad_get<(c + 1) & 3>(quad[q]);                   \
             f[q] = Bits16<T>::to_float(b);                                                   \
         }                                                                                    \
-        collide_lean<float, RHO0>(f, p);                                                     \
+        collide_any<float, RHO0, MRT>(f, p);                                                 \
         _Pragma("unroll") for (int q = 0; q < Q; ++q)                                        \
         {                                                                                    \
             if (SHIFTED && CX(q) > 0) carry[q] = quad_get<c>(quad[q]);                        \
@@ -546,7 +553,7 @@ __device__ __forceinline__ void collide4(uint2 (&quad)[Q], unsigned int (&carry)
 // shared by four cells.  The quads are kept as raw 16-bit codes and the four
 // results are written back into them.  Bitwise the same results as the one-
 // and two-cell kernels.
-template <typename T, bool RHO0, bool WALLS>
+template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Geo g, Relax<float> p)
 {
     const int lane = threadIdx.x & 31;
@@ -563,7 +570,7 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
     load4<false>(src, s, g, lane, last, active, quad, e);
     shuffle4(quad, e, lane, last, carry, right);
     if (!active) return;
-    collide4<T, RHO0, WALLS, true>(quad, carry, right, s, p);
+    collide4<T, RHO0, WALLS, true, MRT>(quad, carry, right, s, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
         *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(dst.p[q]) + s.own + xs) = quad[q];
@@ -573,7 +580,7 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
 // q in, own quads of plane qbar out.  The in-place steps run four blocks per
 // SM (128 registers): at five the spills cost more than the occupancy gains
 // (0.77 against 0.84 of the copy bandwidth measured for the pair of steps).
-template <typename T, bool RHO0>
+template <typename T, bool RHO0, bool MRT = false>
 __global__ void __launch_bounds__(128, 4) k_aa_even4(Planes<T> P, Geo g, Relax<float> p)
 {
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(128, 4) k_aa_even4(Planes<T> P, Geo g, Relax<f
         carry[q] = right[q] = 0u;  // unused: every input of the even step is the own element
     }
     const Site<false> s(x0, y, z, 4, g);
-    collide4<T, RHO0, false, false>(quad, carry, right, s, p);
+    collide4<T, RHO0, false, false, MRT>(quad, carry, right, s, p);
     int own_w = own;
     opaque(own_w);
 #pragma unroll
@@ -608,7 +615,7 @@ __global__ void __launch_bounds__(128, 4) k_aa_even4(Planes<T> P, Geo g, Relax<f
 // quad goes to plane qbar of the own cells.  Each location is written by one
 // thread, and read (for a value that is used) only by that thread, as in the
 // one-cell kernel.
-template <typename T, bool RHO0, bool WALLS>
+template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(128, 4) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p)
 {
     const int lane = threadIdx.x & 31;
@@ -624,7 +631,7 @@ __global__ void __launch_bounds__(128, 4) k_aa_odd4(Planes<T> P, Geo g, Relax<fl
     unsigned int e[Q], carry[Q], right[Q];
     load4<true>(P, s, g, lane, last, active, quad, e);
     shuffle4(quad, e, lane, last, carry, right);
-    if (active) collide4<T, RHO0, WALLS, true>(quad, carry, right, s, p);
+    if (active) collide4<T, RHO0, WALLS, true, MRT>(quad, carry, right, s, p);
     Site<WALLS> sw = s;
     opaque(sw);
 #pragma unroll
@@ -689,8 +696,9 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
     using R = typename Storage<T>::R;
     const Relax<R> p = to_relax<R>(cb);
     const dim3 block(ls.bx, ls.by, 1);
-    if (cb.mrt) {
-        // MRT: one cell per thread
+    const bool quads = sizeof(T) == 2 && ls.cells_x == 4 && (g.nx % 4) == 0;
+    if (cb.mrt && !quads) {
+        // MRT: one cell per thread (16-bit storage with nx % 4 == 0 takes the four-cell kernels below)
         const dim3 grid1((g.nx + ls.bx - 1) / ls.bx, (g.ny + ls.by - 1) / ls.by, g.nz);
         const Planes<T> D = planes_of<T>(dst, g.ncell);
         if (kind == 0)
@@ -701,7 +709,6 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
             k_aa_odd1<T, RHO0, WALLS, true><<<grid1, block, 0, stream>>>(D, g, p);
         return cudaGetLastError();
     }
-    const bool quads = sizeof(T) == 2 && ls.cells_x == 4 && (g.nx % 4) == 0;
     const bool pairs = !quads && ls.cells_x >= 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
     if (quads) {
         // 128 threads; as many along x as one row needs (a multiple of 32), the rest along y
@@ -710,12 +717,20 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
         const dim3 grid4((g.nx + 4 * bx - 1) / (4 * bx), (g.ny + block4.y - 1) / block4.y, g.nz);
         if constexpr (sizeof(T) == 2) {
             const Planes<T> D = planes_of<T>(dst, g.ncell);
-            if (kind == 0)
+            if (cb.mrt) {
+                if (kind == 0)
+                    k_ab4<T, RHO0, WALLS, true><<<grid4, block4, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
+                else if (kind == 1)
+                    k_aa_even4<T, RHO0, true><<<grid4, block4, 0, stream>>>(D, g, p);
+                else
+                    k_aa_odd4<T, RHO0, WALLS, true><<<grid4, block4, 0, stream>>>(D, g, p);
+            } else if (kind == 0) {
                 k_ab4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
-            else if (kind == 1)
+            } else if (kind == 1) {
                 k_aa_even4<T, RHO0><<<grid4, block4, 0, stream>>>(D, g, p);
-            else
+            } else {
                 k_aa_odd4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(D, g, p);
+            }
         }
         return cudaGetLastError();
     }
