@@ -553,9 +553,8 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
 }
 
 // AA even step for 16-bit storage, four cells per thread: own quads of plane
-// q in, own quads of plane qbar out.  The in-place steps run four blocks per
-// SM (128 registers): at five the spills cost more than the occupancy gains
-// (0.77 against 0.84 of the copy bandwidth measured for the pair of steps).
+// q in, own quads of plane qbar out.  Four blocks per SM (128 registers): at
+// five this step spills.  The odd step runs five (measured faster, BF16 most).
 template <typename T, bool RHO0, bool MRT = false>
 __global__ void __launch_bounds__(128, 4) k_aa_even4(Planes<T> P, Geo g, Relax<float> p)
 {
@@ -588,7 +587,7 @@ __global__ void __launch_bounds__(128, 4) k_aa_even4(Planes<T> P, Geo g, Relax<f
 // thread, and read (for a value that is used) only by that thread, as in the
 // one-cell kernel.
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
-__global__ void __launch_bounds__(128, 4) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p)
+__global__ void __launch_bounds__(128, 5) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p)
 {
     const int lane = threadIdx.x & 31;
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
