@@ -116,6 +116,55 @@ def test_shear_wave_256_fp32(collision):
     assert max(r[3] for r in rows) < FP32_LONG_TOL
 
 
+@pytest.mark.parametrize("precision", ["f16s", "bf16s"])
+def test_shear_wave_256_16bit(precision):
+    """The shear-wave workload (periodic 256^3, 2000 steps, SRT, tau = 0.8) with
+    16-bit shifted storage: velocity-field error against the FP64 oracle column,
+    decay-rate and phase errors against nu k^2 and U (stated, as the FP32 test
+    does), for U in {0, 0.1} and both equilibria.  Measured: the viscous change
+    of the shifted populations per step (about 1e-7) is below their 16-bit
+    spacing (about 1e-6 for FP16), so with round-to-nearest storage the wave does
+    not decay at U = 0 (decay-rate error -100 %, u_y error 13 %); with U = 0.1
+    FP16 stays within 2 % of the oracle in u and 10-16 % in u_y, BF16 loses the
+    wave.  The test asserts the exact column structure, finiteness and the
+    FP16/BF16 error levels measured, as a guard against regressions."""
+    n, steps, tau = 256, 2000, 0.8
+    k = 2 * math.pi / n
+    nu = (tau - 0.5) / 3
+    worst = 0.0
+    for U in (0.0, 0.1):
+        for equilibrium in ("standard", "improved"):
+            kw = dict(equilibrium=equilibrium, collision="srt", tau=tau)
+            rho, u = inputs.shear_wave(n, n, n, U=(U, 0, 0), amplitude=0.01, device="cuda")
+            sim = _sim(n, n, n, precision=precision, **kw)
+            sim.init(rho, u.float())
+            del rho, u
+            sim.step(steps)
+            _, ug = sim.moments(torch.float32)
+            col = ug[:, 0:1, 0:1, :]
+            assert torch.equal(ug, col.expand_as(ug)), "columns differ"
+            col = col[:, 0, 0, :].double().cpu().numpy()
+            del ug
+            sim.close()
+            cfg = oracle_config(n, 1, 1, **kw)
+            r1, u1 = inputs.shear_wave(n, 1, 1, U=(U, 0, 0), amplitude=0.01)
+            _, uo = oracle.run(cfg, r1.numpy(), u1.numpy(), steps)
+            uo = uo[:, 0, 0, :]
+            err = rel_maxnorm(col, uo)
+            err_y = float(np.abs(col[1] - uo[1]).max() / np.abs(uo[1]).max())
+            amp, ph = _shear_amp_phase(col[1], n)
+            rate_err = (math.log(0.01 / amp) / steps) / (nu * k * k) - 1
+            ph_err = (ph + math.pi / 2 + k * U * steps + math.pi) % (2 * math.pi) - math.pi
+            amp_o, ph_o = _shear_amp_phase(uo[1], n)
+            rate_err_o = (math.log(0.01 / amp_o) / steps) / (nu * k * k) - 1
+            print("shear256 %s U=%.2f %-8s |u-u_oracle|/|u| %.2e, u_y alone %.2e; decay-rate err %+.3e "
+                  "(oracle %+.3e), phase err %+.3e rad" % (precision, U, equilibrium, err, err_y, rate_err,
+                                                           rate_err_o, ph_err))
+            assert np.isfinite(col).all()
+            worst = max(worst, err)
+    assert worst < (0.15 if precision == "f16s" else 0.2)
+
+
 # ------------------------------------------------------------------ channel 512x256x256
 
 @pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s"])
