@@ -14,14 +14,18 @@
 // are formed once per thread.  WALLS = false compiles the periodic lattice
 // without any bounce-back logic.
 //
-// Two thread mappings:
-//  - one cell per thread (any nx): scalar loads; the +-x populations are read
-//    one element off alignment, which L1/L2 absorb without extra DRAM traffic.
+// Three thread mappings:
+//  - one cell per thread (any nx; the FP32 and FP64 default): scalar loads;
+//    the +-x populations are read one element off alignment, which L1/L2
+//    absorb without extra DRAM traffic.
 //  - two neighbouring cells per thread (nx even): every population is read
 //    and written as an aligned pair (half2 / bfloat162 / float2 / double2);
 //    a +-x shifted pair is assembled from the own pair and one element of the
 //    neighbouring lane's pair (warp shuffle), with one scalar access at the
-//    warp's edge.  Halves the load/store instructions and the index work.
+//    warp's edge.
+//  - four cells per thread (16-bit storage, nx % 4 == 0; the 16-bit default):
+//    8-byte quads of raw 16-bit codes; a +-x shifted window is formed from the
+//    aligned quad and its aligned neighbour quad by funnel shifts (load4w).
 #pragma once
 
 #include "lbm_device.cuh"
