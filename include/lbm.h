@@ -110,7 +110,7 @@ typedef struct lbm_ctx *lbm_handle;
                                  accesses; nx even, bx a multiple of 32); or 4 (16-bit storage,
                                  A/B and AA, nx a multiple of 4, 128-thread blocks shaped from
                                  nx; otherwise treated as 2).  Default 4 for 16-bit storage, 1
-                                 otherwise.  LBM_MRT always runs one cell per thread. */
+                                 otherwise.  LBM_MRT runs one cell per thread except with 4. */
 #define LBM_OPT_MRT_OMEGA_BULK 16 /* LBM_MRT: rate of the trace of the second-order moments
                                      (bulk viscosity (2/9)(1/omega - 1/2)); 0 < v < 2, default 1 */
 #define LBM_OPT_MRT_OMEGA_4    17 /* LBM_MRT: rate of the fourth-order moments; 0 < v < 2,
