@@ -235,6 +235,49 @@ def variant_mlups(args, n, **kw):
     return out
 
 
+def config_variants(peak):
+    """Throughput on the other workload configurations, each on its own lattice:
+    the walled channel 512x256x256 (TRT 3/16, tau 0.6, body force, FP32 / FP16S /
+    BF16S, A/B) and decaying turbulence at 768^3 (SRT, tau 0.51, FP32 / FP16S,
+    in-place AA as the memory-lean pattern for that size)."""
+    import torch
+
+    from paper_1803_04937_gb300 import inputs
+    from paper_1803_04937_gb300.lbm import Simulation
+    out = {}
+    nu = (0.6 - 0.5) / 3
+    a = 8 * nu * 0.05 / 256 ** 2
+    for prec in ("f32", "f16s", "bf16s"):
+        sim = Simulation(512, 256, 256, equilibrium="improved", collision="trt", tau=0.6, precision=prec,
+                         force=(a, 0.0, 0.0), walls=(False, True, False))
+        rho, u = inputs.rest(512, 256, 256, device="cuda")
+        sim.init(rho, u.float() if prec != "f64" else u)
+        del rho, u
+        t = time_steps(sim, 200, 10)
+        cells = 512 * 256 * 256
+        out["channel_512x256x256_" + prec] = {"mlups": cells / t / 1e6,
+                                              "gbs": BYTES_PER_LUP[prec] * cells / t / 1e9}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    n = 768
+    _, u = inputs.hit_spectrum(n, n, n, u_rms=0.04, seed=4, device="cuda")
+    u = u.float()
+    for prec in ("f32", "f16s"):
+        sim = Simulation(n, n, n, equilibrium="improved", collision="srt", tau=0.51, precision=prec, pattern="aa")
+        sim.init(None, u)
+        t = time_steps(sim, 64, 4)
+        out["hit_768_aa_" + prec] = {"mlups": n ** 3 / t / 1e6, "gbs": BYTES_PER_LUP[prec] * n ** 3 / t / 1e9}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    del u
+    torch.cuda.empty_cache()
+    for v in out.values():
+        v["frac"] = v["gbs"] / peak
+    return out
+
+
 def adjoint_ratio(args, n=128, horizon=400):
     """Adjoint cost on the adjoint workload's lattice (periodic n^3, FP32, SRT,
     D3Q19-I, tau = 0.7): per-step kernel times, and the whole differentiable
@@ -484,6 +527,7 @@ def run_native(args):
         variants["d3q27_" + args.precision]["d3q19_speedup_over_d3q27"] = value / variants["d3q27_" + args.precision][
             "mlups"]
         line["variants"] = variants
+        line["configs"] = config_variants(peak)
         line["adjoint"] = adjoint_ratio(args)
     elif rank == 0:
         line["e2e"] = None

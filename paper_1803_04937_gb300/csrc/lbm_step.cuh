@@ -684,8 +684,19 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
     }
     const bool pairs = !quads && ls.cells_x >= 2 && (g.nx % 2) == 0 && (ls.bx % 32) == 0;
     if (quads) {
-        // 128 threads; as many along x as one row needs (a multiple of 32), the rest along y
-        const int bx = min(128, max(32, ((g.nx / 4 + 31) / 32) * 32));
+        // 128 threads; bx in {128, 64, 32} along x (whole warps per row segment), the
+        // rest along y; bx leaves the fewest idle lanes at the end of a row (nx = 768:
+        // 64, so three blocks cover the 192 quads of a row instead of two with 64
+        // idle lanes), the larger on ties
+        const int nq = g.nx / 4;
+        int bx = 128, idle = (nq + 127) / 128 * 128 - nq;
+        for (int c = 64; c >= 32; c /= 2) {
+            const int w = (nq + c - 1) / c * c - nq;
+            if (w < idle) {
+                bx = c;
+                idle = w;
+            }
+        }
         const dim3 block4(bx, 128 / bx, 1);
         const dim3 grid4((g.nx + 4 * bx - 1) / (4 * bx), (g.ny + block4.y - 1) / block4.y, g.nz);
         if constexpr (sizeof(T) == 2) {
