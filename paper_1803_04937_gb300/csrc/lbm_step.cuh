@@ -540,6 +540,19 @@ __device__ __forceinline__ void collide4(uint2 (&win)[Q], const Relax<float> &p)
 // (neighbour elements by warp shuffles and a carry chain through the four
 // cells) took this step from 0.88 to 1.04 of the measured copy bandwidth.
 // Bitwise the same results as the one- and two-cell kernels.
+// Loads, four collisions and stores of k_ab4 for one thread's quad.
+template <typename T, bool RHO0, bool WALLS, bool MRT>
+__device__ __forceinline__ void ab4_body(const Planes<T> &src, const Planes<T> &dst, const Site<WALLS> &s,
+                                         const Geo &g, const Relax<float> &p)
+{
+    uint2 win[Q];
+    load4w<false>(src, s, g, win);
+    collide4<T, RHO0, MRT>(win, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(dst.p[q]) + s.own + s.x) = win[q];
+}
+
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Geo g, Relax<float> p)
 {
@@ -547,13 +560,18 @@ __global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Ge
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (y >= g.ny || x0 >= g.nx) return;  // no lane needs another lane's data
-    const Site<WALLS> s(x0, y, z, 4, g);
-    uint2 win[Q];
-    load4w<false>(src, s, g, win);
-    collide4<T, RHO0, MRT>(win, p);
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-        *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(dst.p[q]) + s.own + x0) = win[q];
+    if constexpr (WALLS) {
+        // A warp covers one row segment; where none of its cells touches a wall
+        // (all but the wall rows and the row ends) it takes the periodic body,
+        // which has no bounce-back selects.  The branch is uniform per warp.
+        const Site<true> sw(x0, y, z, 4, g);
+        const bool touches = sw.bxm || sw.bxp || sw.bym || sw.byp || sw.bzm || sw.bzp;
+        if (__any_sync(__activemask(), touches)) {
+            ab4_body<T, RHO0, true, MRT>(src, dst, sw, g, p);
+            return;
+        }
+    }
+    ab4_body<T, RHO0, false, MRT>(src, dst, Site<false>(x0, y, z, 4, g), g, p);
 }
 
 // AA even step for 16-bit storage, four cells per thread: own quads of plane
