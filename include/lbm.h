@@ -200,7 +200,14 @@ int lbm_bind(lbm_handle h, void *pdf_a, void *pdf_b, void *scratch, void *stream
  */
 int lbm_init(lbm_handle h, const void *rho, const void *u, int dtype);
 
-/* Enqueues n >= 0 time steps of Eq. 15 (stream + collide) on the bound stream. */
+/*
+ * Enqueues n >= 0 time steps of Eq. 15 (stream + collide) on the bound stream.
+ * A caller may capture these launches into its own CUDA graph by capturing
+ * the bound stream (the library then launches plain kernels, see
+ * LBM_OPT_GRAPHS); a replayed capture advances the state but not the step
+ * counter of lbm_steps_done, and an even n keeps the grid / parity bookkeeping
+ * of the handle consistent across replays.
+ */
 int lbm_step(lbm_handle h, int n);
 
 /*
