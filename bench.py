@@ -520,6 +520,7 @@ def run_native(args):
         variants["mrt_f16s"] = variant_mlups(args, n, collision="mrt", precision="f16s")
         variants["standard_" + args.precision] = variant_mlups(args, n, equilibrium="standard")
         variants["d3q27_" + args.precision] = variant_mlups(args, n, equilibrium="standard", stencil=27)
+        variants["d3q27_f16s"] = variant_mlups(args, n, equilibrium="standard", stencil=27, precision="f16s")
         for k, v in variants.items():
             v["frac"] = v["gbs"] / peak
         variants["f16s"]["speedup_vs_main"] = variants["f16s"]["mlups"] / value

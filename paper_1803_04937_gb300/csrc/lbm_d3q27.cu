@@ -2,7 +2,8 @@
 // construction of Sec. 3.1 gives the standard equilibrium of Eq. 14, so both
 // equilibrium choices run Eq. 14), for the paper's D3Q19 / D3Q27 comparison:
 // the same A/B pull scheme, force, TRT, boundaries and storage precisions as
-// the D3Q19 path, with 27 loads + 27 stores per cell.  One cell per thread.
+// the D3Q19 path, with 27 loads + 27 stores per cell.  One cell per thread,
+// or four for 16-bit storage.
 //
 // Also: initialisation f = feq(rho, u), moments and canonical copies for
 // D3Q27 lattices.  (Reductions, AA and the adjoint are D3Q19 only.)
@@ -171,6 +172,80 @@ __global__ void __launch_bounds__(256) k27_ab1(const T *__restrict__ src, T *__r
     for (int q = 0; q < Q27; ++q) Storage<T>::store(dst + (long long)q * g.ncell + s.own + x, f[q]);
 }
 
+// A/B pull step for 16-bit storage, four cells per thread (nx % 4 == 0): the
+// same windowed quads as the D3Q19 four-cell step (each +-x shifted window
+// formed by funnel shifts from the aligned quad and its aligned neighbour),
+// 27 populations.  Bitwise the same results as k27_ab1.
+template <typename T, bool RHO0, bool WALLS>
+__global__ void __launch_bounds__(128, 4) k27_ab4(const T *__restrict__ src, T *__restrict__ dst, Geo g,
+                                                  Relax27<float> p)
+{
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny || x0 >= g.nx) return;
+    const Site<WALLS> s(x0, y, z, 4, g);
+    const int xprev = x0 == 0 ? g.nx - 4 : x0 - 4;
+    const int xnext = x0 + 4 >= g.nx ? 0 : x0 + 4;
+    const unsigned short *base = reinterpret_cast<const unsigned short *>(src);
+    uint2 win[Q27], nb[Q27];
+#pragma unroll
+    for (int q = 0; q < Q27; ++q) {
+        const int cx = CX(q), cy = CY(q), cz = CZ(q);
+        bool w = false;
+        if (WALLS) {
+            if (cy > 0) w |= s.bym;
+            if (cy < 0) w |= s.byp;
+            if (cz > 0) w |= s.bzm;
+            if (cz < 0) w |= s.bzp;
+        }
+        const unsigned short *plane = base + (long long)q * g.ncell + s.row[1 - cy][1 - cz];
+        const unsigned short *bnc = base + (long long)OPP(q) * g.ncell + s.own;
+        const uint2 *pq = reinterpret_cast<const uint2 *>(w ? bnc + x0 : plane + x0);
+        const uint2 *pn = reinterpret_cast<const uint2 *>(plane + (cx > 0 ? xprev : xnext));
+        const bool xwall = WALLS && ((cx > 0 && s.bxm) || (cx < 0 && s.bxp));
+        if (xwall && !w) pn = reinterpret_cast<const uint2 *>(bnc + x0);
+        win[q] = __ldg(pq);
+        if (cx != 0) nb[q] = w ? make_uint2(0u, 0u) : __ldg(pn);
+    }
+#pragma unroll
+    for (int q = 0; q < Q27; ++q) {
+        const int cx = CX(q), cy = CY(q), cz = CZ(q);
+        bool w = false;
+        if (WALLS) {
+            if (cy > 0) w |= s.bym;
+            if (cy < 0) w |= s.byp;
+            if (cz > 0) w |= s.bzm;
+            if (cz < 0) w |= s.bzp;
+        }
+        if (cx == 0 || w) continue;
+        const uint2 c = win[q];
+        uint2 n = nb[q];
+        if (cx > 0) {
+            if (WALLS && s.bxm) n.y = n.x << 16;
+            win[q].x = __funnelshift_l(n.y, c.x, 16);
+            win[q].y = __funnelshift_l(c.x, c.y, 16);
+        } else {
+            if (WALLS && s.bxp) n.x = n.y >> 16;
+            win[q].x = __funnelshift_r(c.x, c.y, 16);
+            win[q].y = __funnelshift_r(c.y, n.x, 16);
+        }
+    }
+#define LBM_AB27_CELL(c)                                                                     \
+    {                                                                                        \
+        float f[Q27];                                                                        \
+        _Pragma("unroll") for (int q = 0; q < Q27; ++q) f[q] = Bits16<T>::to_float(quad_get<c>(win[q]));   \
+        collide27<float, RHO0>(f, p);                                                        \
+        _Pragma("unroll") for (int q = 0; q < Q27; ++q) quad_set<c>(win[q], Bits16<T>::from_float(f[q]));  \
+    }
+    LBM_AB27_CELL(0) LBM_AB27_CELL(1) LBM_AB27_CELL(2) LBM_AB27_CELL(3)
+#undef LBM_AB27_CELL
+    unsigned short *out = reinterpret_cast<unsigned short *>(dst);
+#pragma unroll
+    for (int q = 0; q < Q27; ++q)
+        *reinterpret_cast<uint2 *>(out + (long long)q * g.ncell + s.own + x0) = win[q];
+}
+
 // Writes the canonical populations fc (f_q(x) - w_q) of cell x into an A/B
 // grid so that the pull gather returns them: plane q at x - c_q, or through a
 // wall plane qbar of x.
@@ -328,6 +403,30 @@ cudaError_t launch_step27(int prec, const void *src, void *dst, const Geo &g, co
         const q27::Relax27<R> p = q27::to_relax27<R>(c);
         const T *a = (const T *)src;
         T *b = (T *)dst;
+        if constexpr (sizeof(T) == 2) {
+            if (s.cells_x == 4 && g.nx % 4 == 0) {
+                // four cells per thread; 128-thread blocks shaped as in the D3Q19 step
+                const int nq = g.nx / 4;
+                int bx = 128, idle = (nq + 127) / 128 * 128 - nq;
+                for (int cw = 64; cw >= 32; cw /= 2) {
+                    const int w = (nq + cw - 1) / cw * cw - nq;
+                    if (w < idle) {
+                        bx = cw;
+                        idle = w;
+                    }
+                }
+                const dim3 bl4(bx, 128 / bx, 1);
+                const dim3 gr4((g.nx + 4 * bx - 1) / (4 * bx), (g.ny + bl4.y - 1) / bl4.y, g.nz);
+                if (c.rho0_is_rho) {
+                    if (walls) q27::k27_ab4<T, true, true><<<gr4, bl4, 0, stream>>>(a, b, g, p);
+                    else q27::k27_ab4<T, true, false><<<gr4, bl4, 0, stream>>>(a, b, g, p);
+                } else {
+                    if (walls) q27::k27_ab4<T, false, true><<<gr4, bl4, 0, stream>>>(a, b, g, p);
+                    else q27::k27_ab4<T, false, false><<<gr4, bl4, 0, stream>>>(a, b, g, p);
+                }
+                return cudaGetLastError();
+            }
+        }
         const dim3 gr = q27_grid(g, s), bl = q27_block(s);
         if (c.rho0_is_rho) {
             if (walls) q27::k27_ab1<T, true, true><<<gr, bl, 0, stream>>>(a, b, g, p);

@@ -41,6 +41,43 @@ def test_d3q27_step_matches_oracle(case, precision, tol, pdf_tol):
     assert np.abs(gpu_pdfs_in_oracle_layout(sim) - f_o).max() < pdf_tol
 
 
+@pytest.mark.parametrize("precision", ["f16s", "bf16s"])
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("shape", [(3, 7, 4), (4, 9, 40), (3, 5, 388), (2, 3, 1040)])
+def test_d3q27_four_cells_is_bitwise(shape, case, precision):
+    """16-bit D3Q27 storage with nx % 4 == 0 runs four cells per thread; the
+    results equal the one-cell kernel bit for bit (ragged warps, row ends,
+    several blocks per row, walls on every axis)."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    kw = CASES[case]
+    rho, u = random_fields(shape, seed=43)
+    nz, ny, nx = shape
+    out = []
+    for cells_x in (4, 1):
+        sim = Simulation(nx, ny, nz, precision=precision, stencil=27, equilibrium="standard", cells_x=cells_x, **kw)
+        sim.init(rho.cuda(), u.float().cuda())
+        sim.step(5)
+        out.append(sim.get_pdfs())
+    assert torch.equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("precision,tol", [("f16s", 2e-3), ("bf16s", 2e-2)])
+def test_d3q27_16bit_storage_error(precision, tol):
+    from paper_1803_04937_gb300.lbm import Simulation
+    kw = CASES[1]
+    shape = (6, 10, 64)
+    rho, u = random_fields(shape, seed=17)
+    sim = Simulation(64, 10, 6, precision=precision, stencil=27, equilibrium="standard", **kw)
+    sim.init(rho.cuda(), u.float().cuda())
+    sim.step(20)
+    _, ug = sim.moments()
+    cfg = oracle_config(64, 10, 6, stencil=27, equilibrium="standard", **kw)
+    _, uo = oracle.run(cfg, rho.numpy(), u.numpy(), 20)
+    err = rel_maxnorm(ug.cpu().numpy(), uo)
+    print("D3Q27 %s: velocity error after 20 steps %.2e" % (precision, err))
+    assert err < tol
+
+
 def test_d3q27_duct_has_no_spurious_currents():
     from paper_1803_04937_gb300 import inputs
     from paper_1803_04937_gb300.lbm import Simulation
