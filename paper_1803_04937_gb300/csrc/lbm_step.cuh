@@ -199,6 +199,19 @@ __device__ __forceinline__ void gather1(const Planes<T> &P, const Site<WALLS> &s
     }
 }
 
+// Gather, collision and stores of k_ab1 for one cell.
+template <typename T, bool RHO0, bool WALLS, bool MRT>
+__device__ __forceinline__ void ab1_body(const Planes<T> &src, const Planes<T> &dst, const Site<WALLS> &s,
+                                         const Relax<typename Storage<T>::R> &p)
+{
+    using R = typename Storage<T>::R;
+    R f[Q];
+    gather1<false>(src, s, f);
+    collide_any<R, RHO0, MRT>(f, p);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Storage<T>::store(dst.p[q] + s.own + s.x, f[q]);
+}
+
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
 {
@@ -207,12 +220,16 @@ __global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Site<WALLS> s(x, y, z, 1, g);
-    R f[Q];
-    gather1<false>(src, s, f);
-    collide_any<R, RHO0, MRT>(f, p);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) Storage<T>::store(dst.p[q] + s.own + x, f[q]);
+    if constexpr (WALLS) {
+        // warps with no cell at a wall take the periodic body (uniform branch per warp)
+        const Site<true> sw(x, y, z, 1, g);
+        const bool touches = sw.bxm || sw.bxp || sw.bym || sw.byp || sw.bzm || sw.bzp;
+        if (__any_sync(__activemask(), touches)) {
+            ab1_body<T, RHO0, true, MRT>(src, dst, sw, p);
+            return;
+        }
+    }
+    ab1_body<T, RHO0, false, MRT>(src, dst, Site<false>(x, y, z, 1, g), p);
 }
 
 // AA even step: own cell only (read plane q, write plane qbar).
