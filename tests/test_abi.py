@@ -127,3 +127,22 @@ def test_mrt_options_and_refusals_on_host(lib):
         assert b"SRT and TRT" in lib.lbm_last_error(h)
     finally:
         lib.lbm_destroy(h)
+
+
+def test_graph_and_block_options_on_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(64, 8, 4, 19, 1, 0, 0.8, 2, ctypes.byref(h)) == _lib.LBM_OK
+    try:
+        v = ctypes.c_double()
+        assert lib.lbm_get_option(h, _lib.OPT_GRAPHS, ctypes.byref(v)) == 0 and v.value == 1.0
+        assert lib.lbm_set_option(h, _lib.OPT_GRAPHS, 0.5) == _lib.LBM_EINVAL
+        assert lib.lbm_set_option(h, _lib.OPT_GRAPHS, 0.0) == 0
+        assert lib.lbm_get_option(h, _lib.OPT_GRAPHS, ctypes.byref(v)) == 0 and v.value == 0.0
+        # 16-bit storage defaults to four cells per thread
+        assert lib.lbm_get_option(h, _lib.OPT_CELLS_X, ctypes.byref(v)) == 0 and v.value == 4.0
+        assert lib.lbm_set_option(h, _lib.OPT_CELLS_X, 3.0) == _lib.LBM_EINVAL
+        assert lib.lbm_set_option(h, _lib.OPT_TAU, 0.5) == _lib.LBM_EINVAL
+        assert lib.lbm_set_option(h, _lib.OPT_TAU, float("nan")) == _lib.LBM_EINVAL
+        assert lib.lbm_step(h, -1) in (_lib.LBM_EINVAL, _lib.LBM_ESTATE)
+    finally:
+        lib.lbm_destroy(h)
