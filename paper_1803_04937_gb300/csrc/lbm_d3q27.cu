@@ -133,8 +133,8 @@ __device__ __forceinline__ void collide27(R g[Q27], const Relax27<R> &p)
         const R nasym = fma(-(P * p.A[cls]), cu, d[k]);
         const R a1 = p.hp * nsym;
         const R b = fma(p.hm, nasym, -p.force[k]);
-        g[q] = (g[q] - a1) - b;
-        g[q + 1] = (g[q + 1] - a1) + b;
+        g[q] = g[q] - (a1 + b);
+        g[q + 1] = g[q + 1] - (a1 - b);
     }
 }
 

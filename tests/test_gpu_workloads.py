@@ -61,13 +61,15 @@ def _shear_amp_phase(uy, n):
 
 
 # FP32 runs against the FP64 oracle: the equilibrium's first moment is exact in
-# FP32 (lbm_device.cuh), so the remaining error is rounding.  The velocity used
-# in the equilibrium is the rounded sum of the stored populations, and the
-# antisymmetric relaxation feeds its rounding error back into the momentum each
-# step (factor omega-); in slowly varying flows these errors are partly
-# coherent, giving ~1e-6 ... 2e-5 of max|u| after thousands of steps (measured
-# and printed below).  The long runs assert 2e-5.
-FP32_LONG_TOL = 2e-5
+# FP32 and every population is updated with a single rounding at its own scale
+# (lbm_device.cuh), so the remaining error is accumulated rounding.  The shear
+# wave stays within 4e-6 of max|u| after 2000 steps (asserted: 1e-5).  The
+# channel starts from rest and grows by the body force: its flow is nearly the
+# same from step to step, so the storage rounding of the slowly growing
+# populations does not average out, and after 5000 steps the profile is within
+# 2e-5 (asserted: 3e-5).
+FP32_LONG_TOL = 1e-5
+FP32_CHANNEL_TOL = 3e-5
 
 
 @pytest.mark.parametrize("collision", ["srt", "trt"])
@@ -196,7 +198,7 @@ def test_channel_512x256x256(precision):
     print("channel %s: u_x profile max-norm rel err vs FP64 oracle after %d steps = %.3e (u_max %.3e)"
           % (precision, steps, err, uo[0].max()))
     if precision == "f32":
-        assert err < FP32_LONG_TOL
+        assert err < FP32_CHANNEL_TOL
         assert np.abs(prof[1:]).max() < 1e-9
 
 
