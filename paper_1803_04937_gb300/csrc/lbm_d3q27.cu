@@ -90,7 +90,9 @@ static inline Relax27<R> to_relax27(const CollBoth &c)
     return r;
 }
 
-template <typename R, bool RHO0>
+// ONE_ROUNDING adds each population's change to g in one rounding, as the
+// D3Q19 collision (relax_pair) does for FP32 and FP64 storage.
+template <typename R, bool RHO0, bool ONE_ROUNDING>
 __device__ __forceinline__ void collide27(R g[Q27], const Relax27<R> &p)
 {
     R s[13], d[13];
@@ -131,10 +133,15 @@ __device__ __forceinline__ void collide27(R g[Q27], const Relax27<R> &p)
         const R sym = p.w[cls] * base + (P * p.K[cls]) * (cu * cu);
         const R nsym = fma(R(-2), sym, s[k]);
         const R nasym = fma(-(P * p.A[cls]), cu, d[k]);
-        const R a1 = p.hp * nsym;
         const R b = fma(p.hm, nasym, -p.force[k]);
-        g[q] = g[q] - (a1 + b);
-        g[q + 1] = g[q + 1] - (a1 - b);
+        if (ONE_ROUNDING) {
+            g[q] = g[q] - fma(p.hp, nsym, b);
+            g[q + 1] = g[q + 1] - fma(p.hp, nsym, -b);
+        } else {
+            const R a1 = p.hp * nsym;
+            g[q] = (g[q] - a1) - b;
+            g[q + 1] = (g[q + 1] - a1) + b;
+        }
     }
 }
 
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(256) k27_ab1(const T *__restrict__ src, T *__r
                               : (long long)q * g.ncell + s.row[1 - cy][1 - cz] + xs;
         f[q] = Storage<T>::load(src + a);
     }
-    collide27<R, RHO0>(f, p);
+    collide27<R, RHO0, one_rounding_v<T>>(f, p);
 #pragma unroll
     for (int q = 0; q < Q27; ++q) Storage<T>::store(dst + (long long)q * g.ncell + s.own + x, f[q]);
 }
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(128, 4) k27_ab4(const T *__restrict__ src, T *
     {                                                                                        \
         float f[Q27];                                                                        \
         _Pragma("unroll") for (int q = 0; q < Q27; ++q) f[q] = Bits16<T>::to_float(quad_get<c>(win[q]));   \
-        collide27<float, RHO0>(f, p);                                                        \
+        collide27<float, RHO0, false>(f, p);                                                 \
         _Pragma("unroll") for (int q = 0; q < Q27; ++q) quad_set<c>(win[q], Bits16<T>::from_float(f[q]));  \
     }
     LBM_AB27_CELL(0) LBM_AB27_CELL(1) LBM_AB27_CELL(2) LBM_AB27_CELL(3)

@@ -477,36 +477,49 @@ struct CellEq {
 // place: g -/+ (omega+/2)(s - 2 sym) -/+ (omega-/2)(d - 2 asym) +/- (1 -
 // omega-/2) F for the two members of each pair; the same result as the
 // textbook form g - omega+ (g+ - geq+) - omega- (g- - geq-) + (1 - omega-/2) F
-// up to rounding order.  The change of each population is formed first (small
-// numbers, small rounding) and added to g in one operation: one rounding at
-// the scale of g instead of two (measured on the 256^3 FP32 shear wave after
-// 2000 steps: worst error against the FP64 oracle 1.1e-5 -> 3.7e-6).
-template <typename R, bool RHO0_IS_RHO, int k>
+// up to rounding order.  With ONE_ROUNDING the change of each population is
+// formed first by one fma (small numbers, small rounding) and added to g in one
+// operation: one rounding at the scale of g instead of two (measured on the
+// 256^3 FP32 shear wave after 2000 steps: worst error against the FP64 oracle
+// 1.1e-5 -> 3.7e-6).  The step kernels take it for FP32 and FP64 storage
+// (one_rounding_v); with 16-bit storage the rounding at the store is 2^13 times
+// coarser than FP32's, so the two-rounding form loses nothing there, and some
+// 16-bit kernels run it faster (walled channel 512x256x256, BF16: 77.8 -> 79.8
+// GLUPS; D3Q27 four cells, FP16: 59.6 -> 62.9).
+template <typename T>
+constexpr bool one_rounding_v = sizeof(T) >= 4;
+
+template <typename R, bool RHO0_IS_RHO, bool ONE_ROUNDING, int k>
 __device__ __forceinline__ void relax_pair(R g[Q], const CellEq<R, RHO0_IS_RHO> &e, const Relax<R> &p)
 {
     constexpr int q = 2 * k + 1;
     R nsym, nasym;
     e.template neq<k>(nsym, nasym);
-    const R a1 = p.hp * nsym;
     const R b = fma(p.hm, nasym, -p.force[k]);
-    g[q] = g[q] - (a1 + b);
-    g[q + 1] = g[q + 1] - (a1 - b);
+    if (ONE_ROUNDING) {
+        g[q] = g[q] - fma(p.hp, nsym, b);
+        g[q + 1] = g[q + 1] - fma(p.hp, nsym, -b);
+    } else {
+        const R a1 = p.hp * nsym;
+        g[q] = (g[q] - a1) - b;
+        g[q + 1] = (g[q + 1] - a1) + b;
+    }
 }
 
-template <typename R, bool RHO0_IS_RHO>
+template <typename R, bool RHO0_IS_RHO, bool ONE_ROUNDING>
 __device__ __forceinline__ void collide_lean(R g[Q], const Relax<R> &p)
 {
     const CellEq<R, RHO0_IS_RHO> e(g, p);
     g[0] = fma(-p.wp, g[0] - e.eq0, g[0]);
-    relax_pair<R, RHO0_IS_RHO, 0>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 1>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 2>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 3>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 4>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 5>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 6>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 7>(g, e, p);
-    relax_pair<R, RHO0_IS_RHO, 8>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 0>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 1>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 2>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 3>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 4>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 5>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 6>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 7>(g, e, p);
+    relax_pair<R, RHO0_IS_RHO, ONE_ROUNDING, 8>(g, e, p);
 }
 
 // MRT collision (Sec. 3.2-3.3) in population space.  The even part of the
@@ -521,7 +534,7 @@ __device__ __forceinline__ void collide_lean(R g[Q], const Relax<R> &p)
 // the Q (rest sum Q, face a Q_a - sum Q, edges normal to c Q_c/2); these are
 // the columns of the inverse moment matrix for those moments.  The odd part
 // relaxes at omega- with the force, exactly as in collide_lean.
-template <typename R, bool RHO0_IS_RHO>
+template <typename R, bool RHO0_IS_RHO, bool ONE_ROUNDING>
 __device__ __forceinline__ void collide_mrt(R g[Q], const Relax<R> &p)
 {
     const CellEq<R, RHO0_IS_RHO> e(g, p);
@@ -560,19 +573,24 @@ __device__ __forceinline__ void collide_mrt(R g[Q], const Relax<R> &p)
         }
         const R a1 = fma(p.hp, ns[k], -corr);
         const R b = fma(p.hm, na[k], -p.force[k]);
-        g[q] = g[q] - (a1 + b);
-        g[q + 1] = g[q + 1] - (a1 - b);
+        if (ONE_ROUNDING) {
+            g[q] = g[q] - (a1 + b);
+            g[q + 1] = g[q + 1] - (a1 - b);
+        } else {
+            g[q] = (g[q] - a1) - b;
+            g[q + 1] = (g[q + 1] - a1) + b;
+        }
     }
 }
 
 // Step collision: the lean SRT/TRT update, or MRT.
-template <typename R, bool RHO0_IS_RHO, bool MRT>
+template <typename R, bool RHO0_IS_RHO, bool MRT, bool ONE_ROUNDING>
 __device__ __forceinline__ void collide_any(R g[Q], const Relax<R> &p)
 {
     if constexpr (MRT)
-        collide_mrt<R, RHO0_IS_RHO>(g, p);
+        collide_mrt<R, RHO0_IS_RHO, ONE_ROUNDING>(g, p);
     else
-        collide_lean<R, RHO0_IS_RHO>(g, p);
+        collide_lean<R, RHO0_IS_RHO, ONE_ROUNDING>(g, p);
 }
 
 // Shifted equilibrium geq_q = feq_q(rho, u) - w_q for all q (lbm_init).

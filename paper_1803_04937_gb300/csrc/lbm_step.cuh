@@ -28,6 +28,8 @@
 //    aligned quad and its aligned neighbour quad by funnel shifts (load4w).
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
@@ -207,7 +209,7 @@ __device__ __forceinline__ void ab1_body(const Planes<T> &src, const Planes<T> &
     using R = typename Storage<T>::R;
     R f[Q];
     gather1<false>(src, s, f);
-    collide_any<R, RHO0, MRT>(f, p);
+    collide_any<R, RHO0, MRT, one_rounding_v<T>>(f, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Storage<T>::store(dst.p[q] + s.own + s.x, f[q]);
 }
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Planes<T> Pw, Geo
     R f[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) f[q] = Storage<T>::load(P.p[q] + own);
-    collide_any<R, RHO0, MRT>(f, p);
+    collide_any<R, RHO0, MRT, one_rounding_v<T>>(f, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Storage<T>::store(Pw.p[OPP(q)] + own, f[q]);
 }
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(256) k_aa_odd1(Planes<T> P, Geo g, Relax<typen
     const Site<WALLS> s(x, y, z, 1, g);
     R f[Q];
     gather1<true>(P, s, f);
-    collide_any<R, RHO0, MRT>(f, p);
+    collide_any<R, RHO0, MRT, one_rounding_v<T>>(f, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int cx = CX(q);
@@ -351,8 +353,8 @@ __global__ void __launch_bounds__(256, 4) k_ab2(Planes<T> src, Planes<T> dst, Ge
     R f0[Q], f1[Q];
     gather2<false>(src, s, g, lane, active, f0, f1);
     if (!active) return;
-    collide_lean<R, RHO0>(f0, p);
-    collide_lean<R, RHO0>(f1, p);
+    collide_lean<R, RHO0, one_rounding_v<T>>(f0, p);
+    collide_lean<R, RHO0, one_rounding_v<T>>(f1, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Pair<T>::store(dst.p[q] + s.own + x0, f0[q], f1[q]);
 }
@@ -369,8 +371,8 @@ __global__ void __launch_bounds__(256) k_aa_even2(Planes<T> P, Geo g, Relax<type
     R f0[Q], f1[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) Pair<T>::load(P.p[q] + own, f0[q], f1[q]);
-    collide_lean<R, RHO0>(f0, p);
-    collide_lean<R, RHO0>(f1, p);
+    collide_lean<R, RHO0, one_rounding_v<T>>(f0, p);
+    collide_lean<R, RHO0, one_rounding_v<T>>(f1, p);
 #pragma unroll
     for (int q = 0; q < Q; ++q) Pair<T>::store(P.p[OPP(q)] + own, f0[q], f1[q]);
 }
@@ -396,8 +398,8 @@ __global__ void __launch_bounds__(256, 2) k_aa_odd2(Planes<T> P, Geo g, Relax<ty
     R f0[Q], f1[Q];
     gather2<true>(P, s, g, lane, active, f0, f1);
     if (active) {
-        collide_lean<R, RHO0>(f0, p);
-        collide_lean<R, RHO0>(f1, p);
+        collide_lean<R, RHO0, one_rounding_v<T>>(f0, p);
+        collide_lean<R, RHO0, one_rounding_v<T>>(f1, p);
     }
     const bool last = lane == 31 || x0 + 2 >= g.nx;
 #pragma unroll
@@ -544,7 +546,7 @@ __device__ __forceinline__ void collide4(uint2 (&win)[Q], const Relax<float> &p)
     {                                                                                        \
         float f[Q];                                                                          \
         _Pragma("unroll") for (int q = 0; q < Q; ++q) f[q] = Bits16<T>::to_float(quad_get<c>(win[q]));   \
-        collide_any<float, RHO0, MRT>(f, p);                                                 \
+        collide_any<float, RHO0, MRT, false>(f, p);                                          \
         _Pragma("unroll") for (int q = 0; q < Q; ++q) quad_set<c>(win[q], Bits16<T>::from_float(f[q]));  \
     }
     LBM_AB4_CELL(0) LBM_AB4_CELL(1) LBM_AB4_CELL(2) LBM_AB4_CELL(3)
@@ -573,8 +575,16 @@ __device__ __forceinline__ void ab4_body(const Planes<T> &src, const Planes<T> &
         *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned short *>(dst.p[q]) + s.own + s.x) = win[q];
 }
 
+// Resident blocks per SM for k_ab4.  The walled FP16 kernel (both code paths
+// inlined) spills at five blocks and runs faster at four with no spills; the
+// walled BF16 kernel is the other way round (walled channel 512x256x256:
+// FP16 82.9 -> 84.5 GLUPS at four, BF16 79.9 -> 74.4).
+template <typename T, bool WALLS>
+constexpr int ab4_blocks = (WALLS && std::is_same_v<T, __half>) ? 4 : 5;
+
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
-__global__ void __launch_bounds__(128, 5) k_ab4(Planes<T> src, Planes<T> dst, Geo g, Relax<float> p)
+__global__ void __launch_bounds__(128, ab4_blocks<T, WALLS>) k_ab4(Planes<T> src, Planes<T> dst, Geo g,
+                                                                    Relax<float> p)
 {
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
