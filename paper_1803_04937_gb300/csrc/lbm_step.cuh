@@ -47,6 +47,14 @@ static inline Planes<T> planes_of(void *base, long long ncell)
     return r;
 }
 
+// The rows an A/B launch covers: y in [y0, y1), z in [z0, z0 + gridDim.z).
+// The four-cell step on a lattice with walls on y and/or z runs its interior
+// rows, whose links cross no wall, through the periodic kernel and only the
+// wall rows through the walled one (split_rows).
+struct Rows {
+    int y0, y1, z0;
+};
+
 // Per-thread lattice geometry: wrapped neighbour coordinates, the nine row
 // offsets of the rows y + dy, z + dz (dy, dz in {-1, 0, 1}) and, with walls,
 // the wall flags of the six faces of the cell(s).
@@ -215,13 +223,14 @@ __device__ __forceinline__ void ab1_body(const Planes<T> &src, const Planes<T> &
 }
 
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
-__global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p)
+__global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g, Relax<typename Storage<T>::R> p,
+                                             Rows r)
 {
     using R = typename Storage<T>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
+    const int y = r.y0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    const int z = r.z0 + (int)blockIdx.z;
+    if (x >= g.nx || y >= r.y1) return;
     if constexpr (WALLS) {
         // warps with no cell at a wall take the periodic body (uniform branch per warp)
         const Site<true> sw(x, y, z, 1, g);
@@ -577,19 +586,21 @@ __device__ __forceinline__ void ab4_body(const Planes<T> &src, const Planes<T> &
 
 // Resident blocks per SM for k_ab4.  The walled FP16 kernel (both code paths
 // inlined) spills at five blocks and runs faster at four with no spills; the
-// walled BF16 kernel is the other way round (walled channel 512x256x256:
-// FP16 82.9 -> 84.5 GLUPS at four, BF16 79.9 -> 74.4).
+// walled BF16 kernel is the other way round (measured with the walled channel
+// 512x256x256 as one walled launch: FP16 82.9 -> 84.5 GLUPS at four, BF16
+// 79.9 -> 74.4).  With split_rows the walled kernel runs only the wall rows,
+// or whole lattices with walls on x.
 template <typename T, bool WALLS>
 constexpr int ab4_blocks = (WALLS && std::is_same_v<T, __half>) ? 4 : 5;
 
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
 __global__ void __launch_bounds__(128, ab4_blocks<T, WALLS>) k_ab4(Planes<T> src, Planes<T> dst, Geo g,
-                                                                    Relax<float> p)
+                                                                    Relax<float> p, Rows r)
 {
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (y >= g.ny || x0 >= g.nx) return;  // no lane needs another lane's data
+    const int y = r.y0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    const int z = r.z0 + (int)blockIdx.z;
+    if (y >= r.y1 || x0 >= g.nx) return;  // no lane needs another lane's data
     if constexpr (WALLS) {
         // A warp covers one row segment; where none of its cells touches a wall
         // (all but the wall rows and the row ends) it takes the periodic body,
@@ -711,6 +722,60 @@ __global__ void __launch_bounds__(128, MRT ? 4 : 5) k_aa_odd4(Planes<T> P, Geo g
 
 // ---------------------------------------------------------------- dispatch
 
+// Calls launch(walled, rows, nz_rows) for the launches of one four-cell A/B
+// step.  A periodic lattice, or one with walls on x, is one launch over all
+// rows.  With walls on y and/or z only, the interior rows (no link crosses a
+// wall) run the periodic kernel and the wall rows the walled one: rows y = 0
+// and ny - 1 over all z, then planes z = 0 and nz - 1 over the interior y;
+// every row is in exactly one launch.  Both kernels compute a cell with the
+// same code as the single walled launch, so the results are bitwise the same.
+// The walled four-cell kernel carries both bodies and spills; keeping it to
+// the wall rows took the walled channel 512x256x256 from 84.3 to 89.1 GLUPS
+// (FP16) and from 80.0 to 86.9 (BF16).
+template <bool WALLS, typename F>
+static void split_rows(const Geo &g, F &&launch)
+{
+    if (!WALLS || g.wall_x) {
+        launch(WALLS, Rows{0, g.ny, 0}, g.nz);
+        return;
+    }
+    const int ylo = g.wall_y ? 1 : 0, yhi = g.wall_y ? g.ny - 1 : g.ny;
+    const int zlo = g.wall_z ? 1 : 0, zhi = g.wall_z ? g.nz - 1 : g.nz;
+    if (yhi > ylo && zhi > zlo) launch(false, Rows{ylo, yhi, zlo}, zhi - zlo);
+    if (g.wall_y) {
+        launch(true, Rows{0, 1, 0}, g.nz);
+        if (g.ny > 1) launch(true, Rows{g.ny - 1, g.ny, 0}, g.nz);
+    }
+    if (g.wall_z && yhi > ylo) {
+        launch(true, Rows{ylo, yhi, 0}, 1);
+        if (g.nz > 1) launch(true, Rows{ylo, yhi, g.nz - 1}, 1);
+    }
+}
+
+// The one-cell A/B step stays one launch over all rows: its walled kernel
+// already runs at the periodic kernel's speed (walled channel 512x256x256,
+// FP32: 45.2 GLUPS as one launch, 44.8 split).
+template <typename T, bool RHO0, bool WALLS, bool MRT>
+static void launch_ab1(const Planes<T> &S, const Planes<T> &D, const Geo &g, const Relax<typename Storage<T>::R> &p,
+                       dim3 block, cudaStream_t stream)
+{
+    const dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+    k_ab1<T, RHO0, WALLS, MRT><<<grid, block, 0, stream>>>(S, D, g, p, Rows{0, g.ny, 0});
+}
+
+template <typename T, bool RHO0, bool WALLS, bool MRT>
+static void launch_ab4(const Planes<T> &S, const Planes<T> &D, const Geo &g, const Relax<float> &p, dim3 block4,
+                       cudaStream_t stream)
+{
+    split_rows<WALLS>(g, [&](bool walled, Rows r, int nzr) {
+        const dim3 grid((g.nx + 4 * block4.x - 1) / (4 * block4.x), (r.y1 - r.y0 + block4.y - 1) / block4.y, nzr);
+        if (walled)
+            k_ab4<T, RHO0, true, MRT><<<grid, block4, 0, stream>>>(S, D, g, p, r);
+        else
+            k_ab4<T, RHO0, false, MRT><<<grid, block4, 0, stream>>>(S, D, g, p, r);
+    });
+}
+
 template <typename T, bool RHO0, bool WALLS>
 static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const CollBoth &cb, LaunchShape ls,
                           cudaStream_t stream)
@@ -724,7 +789,7 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
         const dim3 grid1((g.nx + ls.bx - 1) / ls.bx, (g.ny + ls.by - 1) / ls.by, g.nz);
         const Planes<T> D = planes_of<T>(dst, g.ncell);
         if (kind == 0)
-            k_ab1<T, RHO0, WALLS, true><<<grid1, block, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
+            launch_ab1<T, RHO0, WALLS, true>(planes_of<T>(src, g.ncell), D, g, p, block, stream);
         else if (kind == 1)
             k_aa_even1<T, RHO0, true><<<grid1, block, 0, stream>>>(D, D, g, p);
         else
@@ -752,13 +817,13 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
             const Planes<T> D = planes_of<T>(dst, g.ncell);
             if (cb.mrt) {
                 if (kind == 0)
-                    k_ab4<T, RHO0, WALLS, true><<<grid4, block4, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
+                    launch_ab4<T, RHO0, WALLS, true>(planes_of<T>(src, g.ncell), D, g, p, block4, stream);
                 else if (kind == 1)
                     k_aa_even4<T, RHO0, true><<<grid4, block4, 0, stream>>>(D, D, g, p);
                 else
                     k_aa_odd4<T, RHO0, WALLS, true><<<grid4, block4, 0, stream>>>(D, g, p);
             } else if (kind == 0) {
-                k_ab4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(planes_of<T>(src, g.ncell), D, g, p);
+                launch_ab4<T, RHO0, WALLS, false>(planes_of<T>(src, g.ncell), D, g, p, block4, stream);
             } else if (kind == 1) {
                 k_aa_even4<T, RHO0><<<grid4, block4, 0, stream>>>(D, D, g, p);
             } else {
@@ -775,7 +840,7 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
         if (pairs)
             k_ab2<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
         else
-            k_ab1<T, RHO0, WALLS><<<grid, block, 0, stream>>>(S, D, g, p);
+            launch_ab1<T, RHO0, WALLS, false>(S, D, g, p, block, stream);
     } else if (kind == 1) {
         if (pairs)
             k_aa_even2<T, RHO0><<<grid, block, 0, stream>>>(D, g, p);
