@@ -243,12 +243,26 @@ __global__ void __launch_bounds__(256) k_ab1(Planes<T> src, Planes<T> dst, Geo g
     ab1_body<T, RHO0, false, MRT>(src, dst, Site<false>(x, y, z, 1, g), p);
 }
 
+// Blocks per SM the one-cell AA steps are compiled for.  With the compensated
+// momentum sum of FP32 storage the compiler's own choice for the odd step is
+// 94 registers, two blocks of 256 threads per SM (FP32 AA pair 0.98 -> 0.83
+// of the copy bandwidth at 256^3).  Measured for the FP32 SRT/TRT pair
+// (even, odd blocks; 256^3 / 768^3): (5, 3) 0.932 / 0.943 (odd step 80
+// registers, 16 bytes spilled; even 48, none), (6, 3) 0.911 / 0.924, (5, 2)
+// 0.889 / 0.897, (6, 4) 0.859 / 0.871; (5, 3) is kept.
+template <typename T, bool MRT>
+constexpr int aa1_blocks(bool odd)
+{
+    return (std::is_same<T, float>::value && !MRT) ? (odd ? 3 : 5) : 1;
+}
+
 // AA even step: own cell only (read plane q, write plane qbar).  The store
 // side takes its own copy of the plane table (the same pointers): given one
 // table, the compiler keeps its 19 pointers in registers between the loads and
 // the stores (80 instead of 40 registers; +1.5 % FP32, +2.8 % FP64 measured).
 template <typename T, bool RHO0, bool MRT = false>
-__global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Planes<T> Pw, Geo g, Relax<typename Storage<T>::R> p)
+__global__ void __launch_bounds__(256, aa1_blocks<T, MRT>(false)) k_aa_even1(Planes<T> P, Planes<T> Pw, Geo g,
+                                                                           Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,7 +282,8 @@ __global__ void __launch_bounds__(256) k_aa_even1(Planes<T> P, Planes<T> Pw, Geo
 // a wall: read plane q / write plane qbar of the own cell).  Every location is
 // read and written by exactly one thread.
 template <typename T, bool RHO0, bool WALLS, bool MRT = false>
-__global__ void __launch_bounds__(256) k_aa_odd1(Planes<T> P, Geo g, Relax<typename Storage<T>::R> p)
+__global__ void __launch_bounds__(256, aa1_blocks<T, MRT>(true)) k_aa_odd1(Planes<T> P, Geo g,
+                                                                         Relax<typename Storage<T>::R> p)
 {
     using R = typename Storage<T>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;

@@ -49,3 +49,74 @@ def rel_maxnorm(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def oracle_run_fp32_storage(cfg, rho, u, nsteps):
+    """The oracle with FP32 storage: every oracle step (FP64 arithmetic) is
+    followed by rounding the shifted populations f_q - w_q to float32, which is
+    what FP32 storage does to the state between steps.  Separates the error
+    that storage alone causes from the error of the GPU's FP32 arithmetic.
+    Returns the final (rho, u)."""
+    _, w, _ = oracle.velocity_set(cfg.stencil)
+    f = oracle.init(cfg, rho, u)
+    f = w + (f - w).astype(np.float32).astype(np.float64)
+    for _ in range(nsteps):
+        f = oracle.step(cfg, f, 1)
+        f = w + (f - w).astype(np.float32).astype(np.float64)
+    return oracle.moments(cfg, f)
+
+
+# ---------------------------------------------------------------- linear stability of uniform flow
+
+def _d3q19_velocities():
+    """D3Q19 velocities and weights enumerated here (rest, faces, edges; Sec. 2.3)."""
+    c = [(0, 0, 0)]
+    c += [v for v in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))]
+    c += [(a, b, 0) for a in (1, -1) for b in (1, -1)]
+    c += [(a, 0, b) for a in (1, -1) for b in (1, -1)]
+    c += [(0, a, b) for a in (1, -1) for b in (1, -1)]
+    c = np.array(c, dtype=np.float64)
+    n2 = (c * c).sum(axis=1)
+    w = np.where(n2 == 0, 1 / 3, np.where(n2 == 1, 1 / 18, 1 / 36))
+    return c, w
+
+
+def srt_collision_jacobian(U, improved, tau):
+    """d f* / d f of one SRT collision (Eq. 15, no force, rho0 = 1) at the
+    equilibrium of rho = 1, u = U, written from the derivatives of Eq. 14
+    (second order) and of the D3Q19-I corrections of Eq. 22 (rest + u^2/6,
+    face along a - (u^2 - u_a^2)/12, edge normal to c + u_c^2/24).  Returns
+    (J, c) with c the velocities in this function's own order."""
+    c, w = _d3q19_velocities()
+    U = np.asarray(U, dtype=np.float64)
+    q = len(w)
+    dfeq_drho = w.copy()
+    dfeq_du = np.zeros((q, 3))
+    for i in range(q):
+        cu = c[i] @ U
+        dfeq_du[i] = w[i] * (3 * c[i] + 9 * cu * c[i] - 3 * U)
+        if improved:
+            n2 = int(c[i] @ c[i])
+            if n2 == 0:
+                dfeq_du[i] += U / 3
+            elif n2 == 1:
+                e = np.abs(c[i])
+                dfeq_du[i] -= (U - U * e) / 6
+            else:
+                e = 1 - np.abs(c[i])  # the axis normal to the edge's plane
+                dfeq_du[i] += U * e / 12
+    E = np.outer(dfeq_drho, np.ones(q)) + dfeq_du @ c.T  # rho = sum f, u = sum c f
+    omega = 1 / tau
+    return np.eye(q) - omega * (np.eye(q) - E), c
+
+
+def srt_max_amplification(U, improved, tau, n):
+    """Largest |eigenvalue| of the linearised stream + collide step over the
+    wave vectors of a periodic n^3 lattice (von Neumann analysis of the
+    uniform flow U)."""
+    J, c = srt_collision_jacobian(U, improved, tau)
+    ks = 2 * np.pi * np.arange(n) / n
+    kk = np.stack(np.meshgrid(ks, ks, ks, indexing="ij"), axis=-1).reshape(-1, 3)
+    ph = np.exp(-1j * (kk @ c.T))  # [nk, Q]
+    G = ph[:, :, None] * J[None, :, :]
+    return float(np.abs(np.linalg.eigvals(G)).max())

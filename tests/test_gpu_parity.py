@@ -105,15 +105,19 @@ def test_aa_four_cells_is_bitwise(shape, case, precision):
         assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
 
 
+@pytest.mark.parametrize("collision", ["trt", "mrt"])
 @pytest.mark.parametrize("precision", ["f16s", "bf16s"])
 @pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True)])
 @pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (6, 3, 1040)])
-def test_four_cell_ab_split_rows_is_bitwise(shape, walls, precision):
+def test_four_cell_ab_split_rows_is_bitwise(shape, walls, precision, collision):
     """With walls on y and/or z only, the four-cell A/B step runs its interior
     rows through the periodic kernel and the wall rows through the walled one
-    (split_rows); the result is bitwise that of the one-cell step, also on
-    lattices of one or two rows or planes, which have no interior."""
-    kw = dict(equilibrium="improved", collision="trt", tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
+    (split_rows), for the TRT and the MRT collision; the result is bitwise that
+    of the one-cell step, also on lattices of one or two rows or planes, which
+    have no interior."""
+    kw = dict(equilibrium="improved", collision=collision, tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
+    if collision == "mrt":
+        kw.update(omega_bulk=1.3, omega_4=0.9)
     rho, u = random_fields(shape, seed=11)
     for steps in (1, 5):
         sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=1)

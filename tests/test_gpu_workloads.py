@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from paper_1803_04937_gb300 import inputs
-from tests._helpers import oracle_config, rel_maxnorm
+from tests._helpers import oracle_config, oracle_run_fp32_storage, rel_maxnorm
 
 pytestmark = pytest.mark.gpu
 
@@ -61,15 +61,13 @@ def _shear_amp_phase(uy, n):
 
 
 # FP32 runs against the FP64 oracle: the equilibrium's first moment is exact in
-# FP32 and every population is updated with a single rounding at its own scale
-# (lbm_device.cuh), so the remaining error is accumulated rounding.  The shear
-# wave stays within 4e-6 of max|u| after 2000 steps (asserted: 1e-5).  The
-# channel starts from rest and grows by the body force: its flow is nearly the
-# same from step to step, so the storage rounding of the slowly growing
-# populations does not average out, and after 5000 steps the profile is within
-# 2e-5 (asserted: 3e-5).
+# FP32, every population is updated with a single rounding at its own scale,
+# and the momentum is summed with compensation so that rounding the velocity
+# does not feed a momentum error back through the relaxation (lbm_device.cuh).
+# What remains is the rounding of the stored populations: the shear waves stay
+# within about 1.5e-6 of max|u| after 2000 steps and the channel (5000 steps
+# from rest) within about 1e-6; both are asserted at the 1e-5 FP32 target.
 FP32_LONG_TOL = 1e-5
-FP32_CHANNEL_TOL = 3e-5
 
 
 @pytest.mark.parametrize("collision", ["srt", "trt"])
@@ -169,12 +167,24 @@ def test_shear_wave_256_16bit(precision):
 
 # ------------------------------------------------------------------ channel 512x256x256
 
+# Profile error of the 16-bit channel runs against the FP64 oracle after 5000
+# steps, as measured (guards against regressions, not targets): FP16 storage
+# cannot hold the per-step force increment of the shifted populations (about
+# 3e-8 against an FP16 spacing of about 6e-8 at 1e-4), so the flow never
+# starts (error 1.0); BF16 stagnates (about 0.82).
+CHANNEL_16BIT_ERR = {"f16s": 1.0 + 1e-6, "bf16s": 0.85}
+
+
 @pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s"])
 def test_channel_512x256x256(precision):
     """Walls at y = -1/2 and 255.5, periodic x, z, body force a_x = 8 nu u_c / H^2
-    (steady centreline 0.05), TRT 3/16, tau = 0.6, 5000 steps: every (x,z) column is
-    bitwise equal; the y profile vs the FP64 oracle's 1x256x1 column: <= 1e-5 for
-    FP32, measured and stated for 16-bit storage."""
+    (steady centreline 0.05), TRT 3/16, tau = 0.6, 5000 steps: every (x,z) column
+    is bitwise equal, and the y profile is compared with the FP64 oracle's
+    1x256x1 column.  FP32: <= 1e-5 against the oracle and <= 1e-5 against the
+    oracle with FP32 storage (FP64 steps, populations rounded to float32 after
+    each step), whose own distance to the oracle (the floor that FP32 storage
+    sets) is printed.  16-bit storage: the measured profile errors
+    (CHANNEL_16BIT_ERR) are asserted as upper bounds."""
     nx, ny, nz, steps, tau = 512, 256, 256, 5000, 0.6
     nu = (tau - 0.5) / 3
     a = 8 * nu * 0.05 / ny ** 2
@@ -198,8 +208,16 @@ def test_channel_512x256x256(precision):
     print("channel %s: u_x profile max-norm rel err vs FP64 oracle after %d steps = %.3e (u_max %.3e)"
           % (precision, steps, err, uo[0].max()))
     if precision == "f32":
-        assert err < FP32_CHANNEL_TOL
+        _, ue = oracle_run_fp32_storage(cfg, r1.numpy(), u1.numpy(), steps)
+        ue = ue[:, 0, :, 0]
+        err_e = rel_maxnorm(prof[0], ue[0])
+        print("channel f32: vs the oracle with FP32 storage %.3e; that emulation vs the oracle %.3e"
+              % (err_e, rel_maxnorm(ue[0], uo[0])))
+        assert err < FP32_LONG_TOL and err_e < FP32_LONG_TOL
         assert np.abs(prof[1:]).max() < 1e-9
+    else:
+        assert np.isfinite(prof).all()
+        assert err <= CHANNEL_16BIT_ERR[precision]
 
 
 def test_poiseuille_steady_profile_on_gpu():
