@@ -1,0 +1,133 @@
+"""The discriminating Galilean-invariance workloads at 256^3 in FP32, D3Q19-S
+against D3Q19-I.
+
+Summed over c_z, the D3Q19-I equilibrium (Eq. 22) is the D2Q9 equilibrium for
+any u_z, and D3Q19-S (Eq. 14) is D2Q9 only when u_z = 0.  So the shear wave of
+the benchmark (u_y(x) on a background U_x) runs identically under both, and
+the difference between them shows in flows that vary along two axes: the
+x-invariant cross shear u = (U + A sin(2 pi y/N) sin(2 pi z/N), 0, 0) is the
+wall-free form of the paper's duct (Sec. 5.1), where the error term of Eq. 39
+(a third derivative of u_x^2 across the flow) drives transverse velocities
+under D3Q19-S and none under D3Q19-I.  A background velocity along the wave's
+third axis (U_z) is checked as well.
+
+Both flows are invariant along one or two axes, so one oracle plane or column
+is an exact sample of the 256^3 run: every GPU slice along the invariant axes
+must be bitwise equal, and the sample is compared with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1803_04937_gb300 import inputs
+from tests._helpers import oracle_config, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def _sim(n, **kw):
+    from paper_1803_04937_gb300.lbm import Simulation
+    return Simulation(n, n, n, precision="f32", **kw)
+
+
+def test_cross_shear_256_fp32():
+    """Cross shear at 256^3, FP32, SRT tau = 1 (Lambda^2 = 1/4, away from the
+    1/12 where the leading S error term vanishes), A = 0.02, U in {0, 0.05,
+    0.1}, 1000 steps: the GPU's x-slices are bitwise equal and match the FP64
+    oracle's 1x256x256 plane to 1e-5; the transverse velocity
+    max(|u_y|, |u_z|) / A is zero in the oracle and at FP32 rounding on the GPU
+    for D3Q19-I at every U, and for D3Q19-S it follows the oracle and grows
+    with U (the U A part of the error term adds to the A^2 part; measured
+    4e-7, 4.6e-6, 9.7e-6 at U = 0, 0.05, 0.1)."""
+    n, steps, A, tau = 256, 1000, 0.02, 1.0
+    ratio = {}
+    for U in (0.0, 0.05, 0.1):
+        for equilibrium in ("standard", "improved"):
+            kw = dict(equilibrium=equilibrium, collision="srt", tau=tau)
+            rho, u = inputs.cross_shear(n, n, n, U=U, amplitude=A, device="cuda")
+            sim = _sim(n, **kw)
+            sim.init(rho, u.float())
+            del rho, u
+            sim.step(steps)
+            _, ug = sim.moments(torch.float32)
+            plane = ug[..., 0:1]
+            assert torch.equal(ug, plane.expand_as(ug)), "x-slices differ"
+            plane = plane[..., 0].double().cpu().numpy()  # [3, nz, ny]
+            del ug
+            sim.close()
+            cfg = oracle_config(1, n, n, **kw)
+            r1, u1 = inputs.cross_shear(1, n, n, U=U, amplitude=A)
+            _, uo = oracle.run(cfg, r1.numpy(), u1.numpy(), steps)
+            uo = uo[..., 0]
+            err = rel_maxnorm(plane, uo)
+            r_gpu = float(np.abs(plane[1:]).max() / A)
+            r_or = float(np.abs(uo[1:]).max() / A)
+            ratio[(equilibrium, U)] = r_gpu
+            print("cross shear 256^3 FP32 U=%.2f %-8s: max|u_yz|/A GPU %.3e, oracle %.3e; |u - u_oracle|/|u| %.2e"
+                  % (U, equilibrium, r_gpu, r_or, err))
+            assert err < FP32_TOL
+            if equilibrium == "improved":
+                assert r_or < 1e-13  # exactly zero up to FP64 rounding
+            else:
+                assert abs(r_gpu - r_or) < 1e-6  # the GPU reproduces the oracle's transverse flow
+    # D3Q19-I: what remains is FP32 rounding of a flow of speed ~U + A (measured
+    # 3e-8 ... 2e-7); D3Q19-S grows with U (the U A part of the Eq. 39 term) and
+    # is well above that floor once the flow moves
+    for U in (0.0, 0.05, 0.1):
+        assert ratio[("improved", U)] < 5e-7
+    for U in (0.05, 0.1):
+        assert ratio[("standard", U)] > 10 * ratio[("improved", U)]
+    assert ratio[("standard", 0.0)] < ratio[("standard", 0.05)] < ratio[("standard", 0.1)]
+
+
+def _amp_phase(uy, n):
+    k = 2 * math.pi / n
+    c = (uy * np.exp(-1j * k * np.arange(n))).sum() * 2 / n
+    return abs(c), np.angle(c)
+
+
+def test_shear_wave_normal_background_256_fp32():
+    """Shear wave u_y = 0.01 sin(2 pi x/256) on a background U_z in {0, 0.05,
+    0.1} (normal to the wave vector and to u_y), 256^3, FP32, SRT tau = 0.8,
+    2000 steps: the (y,z) columns are bitwise equal and match the FP64 oracle
+    column to 1e-5, and (u_x, u_y) is the same as with U_z = 0 to FP32 rounding
+    under both equilibria.  For D3Q19-I this is exact (its c_x, c_y projection
+    is D2Q9 for any u_z); for D3Q19-S the u_z^2 terms by which it differs from
+    D2Q9 are uniform here and change no hydrodynamic moment.  Prints the decay
+    rate error against nu k^2."""
+    n, steps, tau = 256, 2000, 0.8
+    k = 2 * math.pi / n
+    nu = (tau - 0.5) / 3
+    cols = {}
+    for equilibrium in ("standard", "improved"):
+        for Uz in (0.0, 0.05, 0.1):
+            kw = dict(equilibrium=equilibrium, collision="srt", tau=tau)
+            rho, u = inputs.shear_wave(n, n, n, U=(0, 0, Uz), amplitude=0.01, device="cuda")
+            sim = _sim(n, **kw)
+            sim.init(rho, u.float())
+            del rho, u
+            sim.step(steps)
+            _, ug = sim.moments(torch.float32)
+            col = ug[:, 0:1, 0:1, :]
+            assert torch.equal(ug, col.expand_as(ug)), "columns differ"
+            col = col[:, 0, 0, :].double().cpu().numpy()
+            del ug
+            sim.close()
+            cfg = oracle_config(n, 1, 1, **kw)
+            r1, u1 = inputs.shear_wave(n, 1, 1, U=(0, 0, Uz), amplitude=0.01)
+            _, uo = oracle.run(cfg, r1.numpy(), u1.numpy(), steps)
+            uo = uo[:, 0, 0, :]
+            err = rel_maxnorm(col[:2], uo[:2])
+            amp, _ = _amp_phase(col[1], n)
+            rate_err = (math.log(0.01 / amp) / steps) / (nu * k * k) - 1
+            cols[(equilibrium, Uz)] = col
+            dev = rel_maxnorm(col[:2], cols[(equilibrium, 0.0)][:2])
+            print("shear wave U_z=%.2f %-8s 256^3 FP32: |(u_x,u_y) - oracle| %.2e, change vs U_z=0 %.2e, "
+                  "decay-rate err %+.3e, |u_z - oracle| %.2e" % (Uz, equilibrium, err, dev, rate_err,
+                                                                 np.abs(col[2] - uo[2]).max()))
+            assert err < FP32_TOL
+            assert dev < FP32_TOL
