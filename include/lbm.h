@@ -196,7 +196,11 @@ int lbm_bind(lbm_handle h, void *pdf_a, void *pdf_b, void *scratch, void *stream
 /*
  * Sets the state to f_q = f_q^eq(rho, u) for the configured equilibrium
  * (Eq. 14 or Eq. 22; no non-equilibrium part) and resets the step counter.
- * rho, u: device buffers of element type dtype; rho may be NULL (rho = 1).
+ * rho, u: buffers of element type dtype; rho may be NULL (rho = 1).  Either
+ * may be device memory or pinned (page-locked) host memory: the kernel then
+ * reads the host buffer directly through its mapped device address, with no
+ * staging copy, and the buffer must stay valid until the stream has passed
+ * the call.  Pageable host memory returns LBM_EINVAL.
  */
 int lbm_init(lbm_handle h, const void *rho, const void *u, int dtype);
 
@@ -212,8 +216,10 @@ int lbm_step(lbm_handle h, int n);
 
 /*
  * Writes rho (Eq. 16) and u (Eq. 17: rho0 u = sum_q c_q f_q + a/2) of the
- * current state into device buffers of element type dtype.  Either output may
- * be NULL.
+ * current state into buffers of element type dtype.  Either output may be
+ * NULL.  As for lbm_init, an output may be device memory or pinned host memory
+ * (written directly by the kernel; complete once the bound stream has passed
+ * the call); pageable host memory returns LBM_EINVAL.
  */
 int lbm_moments(lbm_handle h, void *rho, void *u, int dtype);
 
@@ -250,9 +256,12 @@ int lbm_enstrophy(lbm_handle h, double *out);
  * not depend on the lattice size, so every lattice lbm_create accepts fits;
  * should the reduction ever need more rows than the array holds, the call
  * returns LBM_EUNSUPPORTED with a message.  It calls no allocating routine.
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and every call
+ * Every call looks the array's device address up (cudaGetSymbolAddress) with
+ * the calling thread's current device, which must be the device of the bound
+ * stream (LBM_EINVAL otherwise); so the address stays right after the caller
+ * has reset the device (cudaDeviceReset) and re-bound fresh buffers.  The
+ * first lookup on a device may load the library's device code; make the
+ * first call on a device before any stream capture.  All calls share the array and every call
  * rewrites the parts it reads, so no clearing is needed, but calls that
  * overlap on the GPU (other streams, other handles) race on it.  Needs
  * lbm_bind (grids and stream; the scratch pointer may be NULL).

@@ -141,6 +141,34 @@ int no_mrt(lbm_handle h, const char *what)
     return fail(h, LBM_EUNSUPPORTED, std::string(what) + " supports SRT and TRT only");
 }
 
+// Address through which the kernels reach a macroscopic field buffer: device
+// (or managed) memory as it is; pinned host memory through its mapped device
+// address, so that lbm_init and lbm_moments read and write host buffers
+// directly over the host link (no staging copy, no device allocation);
+// pageable host memory is refused.  NULL stays NULL.
+int field_address(lbm_handle h, const void *p, const char *name, const void **out)
+{
+    *out = nullptr;
+    if (!p) return LBM_OK;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) return cuda_fail(h, e, name);
+    switch (a.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+        *out = p;
+        return LBM_OK;
+    case cudaMemoryTypeHost:
+        if (!a.devicePointer)
+            return fail(h, LBM_EINVAL, std::string(name) + ": pinned host memory without a device mapping");
+        *out = a.devicePointer;
+        return LBM_OK;
+    default:
+        return fail(h, LBM_EINVAL, std::string(name) + ": pageable host memory (pass device memory or pinned "
+                                                       "host memory)");
+    }
+}
+
 int check_dtype(lbm_handle h, int dtype)
 {
     if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return fail(h, LBM_EINVAL, "dtype must be LBM_DTYPE_F64 or LBM_DTYPE_F32");
@@ -422,6 +450,11 @@ int lbm_init(lbm_handle h, const void *rho, const void *u, int dtype)
     if (s) return s;
     if ((s = check_dtype(h, dtype))) return s;
     if (!u) return fail(h, LBM_EINVAL, "u is NULL");
+    const void *rho_d, *u_d;
+    if ((s = field_address(h, rho, "lbm_init rho", &rho_d))) return s;
+    if ((s = field_address(h, u, "lbm_init u", &u_d))) return s;
+    rho = rho_d;
+    u = u_d;
     h->parity = 0;
     cudaError_t e = h->stencil == LBM_D3Q27
                         ? lbm::launch_init27(h->precision, current(h), rho, u, dtype, geo(h), coll(h), h->stream)
@@ -478,6 +511,11 @@ int lbm_moments(lbm_handle h, void *rho, void *u, int dtype)
     if ((s = check_dtype(h, dtype))) return s;
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
     if (!rho && !u) return LBM_OK;
+    const void *rho_d, *u_d;
+    if ((s = field_address(h, rho, "lbm_moments rho", &rho_d))) return s;
+    if ((s = field_address(h, u, "lbm_moments u", &u_d))) return s;
+    rho = const_cast<void *>(rho_d);
+    u = const_cast<void *>(u_d);
     cudaError_t e = h->stencil == LBM_D3Q27
                         ? lbm::launch_moments27(h->precision, current(h), rho, u, dtype, geo(h), coll(h), h->stream)
                         : lbm::launch_moments(h->precision, layout(h), current(h), rho, u, dtype, geo(h), coll(h),
@@ -539,6 +577,9 @@ int lbm_reduce_noalloc(lbm_handle h, double *out)
     double *result = nullptr;
     cudaError_t e = lbm::launch_reduce_noalloc(h->precision, layout(h), current(h), geo(h), coll(h), h->stream,
                                                &result);
+    if (e == cudaErrorInvalidDevice)
+        return fail(h, LBM_EINVAL, "lbm_reduce_noalloc: the calling thread's current device is not the device of "
+                                   "the bound stream");
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_reduce_noalloc");
     e = cudaMemcpyAsync(out, result, LBM_RED_COUNT * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_reduce_noalloc copy");

@@ -1,7 +1,6 @@
 // Kernels around the time step: initialisation f = feq(rho, u), macroscopic
 // moments (Eq. 16, Eq. 17), canonical copies of the state, and the FP64
 // global reductions (mass, kinetic energy, momentum, max |u|, non-finite count).
-#include <mutex>
 
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
@@ -347,19 +346,19 @@ cudaError_t launch_reduce(int prec, int layout, const void *grid, double *scratc
 // in this file-scope array instead of the scratch buffer lent to lbm_bind.
 // Every GPU that loads the library holds the array until the process exits.
 // In host code `g_reduce_scratch` only names a host-side stand-in; the device
-// address is looked up once per device with cudaGetSymbolAddress (the first
-// call on a device does it, so that first call should come before any stream
-// capture).  All calls share the array and each call overwrites all of it
-// that it reads (every block writes its partial row, the final kernel writes
-// the results), so nothing needs clearing between calls; calls that overlap
-// on the GPU (several streams or handles at once) race on it.
+// address is looked up with cudaGetSymbolAddress on every call, with the
+// calling thread's current device, which must be the device of the bound
+// stream (checked).  Looking it up each time keeps it right after the
+// primary context has been destroyed and created again (cudaDeviceReset); the
+// first lookup on a device may load the library's module, so the first call
+// on a device should come before any stream capture.  All calls share the
+// array and each call overwrites all of it that it reads (every block writes
+// its partial row, the final kernel writes the results), so nothing needs
+// clearing between calls; calls that overlap on the GPU (several streams or
+// handles at once) race on it.
 constexpr int NOALLOC_MAX_BLOCKS = 1024;                 // partial rows the array holds
 constexpr int NOALLOC_DOUBLES = NOALLOC_MAX_BLOCKS * 8 + 8;  // 64 KiB + results
 static __device__ __align__(256) double g_reduce_scratch[NOALLOC_DOUBLES];
-
-static std::mutex g_reduce_scratch_mu;
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static double *g_reduce_scratch_dev[NOALLOC_MAX_DEVICES];
 
 int reduce_noalloc_capacity_doubles() { return NOALLOC_DOUBLES; }
 
@@ -385,21 +384,16 @@ cudaError_t launch_reduce_noalloc(int prec, int layout, const void *grid, const 
                                   cudaStream_t s, double **result)
 {
     if ((long long)RED_BLOCKS * 8 + 8 > NOALLOC_DOUBLES) return cudaErrorInvalidValue;
-    int dev = -1;
+    int dev = -1, sdev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    double *base;
-    {
-        std::lock_guard<std::mutex> lock(g_reduce_scratch_mu);
-        if (!g_reduce_scratch_dev[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_reduce_scratch);
-            if (e != cudaSuccess) return e;
-            g_reduce_scratch_dev[dev] = (double *)p;
-        }
-        base = g_reduce_scratch_dev[dev];
-    }
+    e = cudaStreamGetDevice(s, &sdev);
+    if (e != cudaSuccess) return e;
+    if (sdev != dev) return cudaErrorInvalidDevice;
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_reduce_scratch);
+    if (e != cudaSuccess) return e;
+    double *base = static_cast<double *>(p);
     *result = base + (size_t)RED_BLOCKS * 8;
     return launch_reduce(prec, layout, grid, base, *result, g, c, s);
 }

@@ -184,25 +184,22 @@ class Simulation:
 
     # -- end to end from host memory -----------------------------------------
     def run_host(self, rho_host, u_host, nsteps, out=None):
-        """End-to-end call from host memory: copies rho, u (pinned host tensors)
-        to the device, initialises, runs nsteps, and copies rho, u back into
-        ``out`` (pinned host tensors) or new host tensors.  Returns (rho, u)."""
-        s = self.stream
-        with torch.cuda.stream(s):
-            u = u_host.to(self.device, non_blocking=True)
-            rho = rho_host.to(self.device, non_blocking=True) if rho_host is not None else None
-            dt = _field_dtype(u)
-            check(self._lib.lbm_init(self._h, _ptr(rho), _ptr(u), dt), self._h)
-            check(self._lib.lbm_step(self._h, int(nsteps)), self._h)
-            rd = torch.empty(self.shape, dtype=u.dtype, device=self.device)
-            ud = torch.empty_like(u)
-            check(self._lib.lbm_moments(self._h, _ptr(rd), _ptr(ud), dt), self._h)
-            if out is None:
-                out = (torch.empty(rd.shape, dtype=rd.dtype, pin_memory=True),
-                       torch.empty(ud.shape, dtype=ud.dtype, pin_memory=True))
-            out[0].copy_(rd, non_blocking=True)
-            out[1].copy_(ud, non_blocking=True)
-        s.synchronize()
+        """End-to-end call from host memory: lbm_init reads rho, u straight from
+        the pinned host tensors (the kernel reaches them through their mapped
+        device address, no staging copy), nsteps steps run, and lbm_moments
+        writes rho, u straight into ``out`` (pinned host tensors, allocated if
+        None).  Synchronises the stream; returns (rho, u)."""
+        for t in (rho_host, u_host) + (tuple(out) if out is not None else ()):
+            if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
+                raise ValueError("run_host takes contiguous pinned host tensors")
+        dt = _field_dtype(u_host)
+        if out is None:
+            out = (torch.empty(self.shape, dtype=u_host.dtype, pin_memory=True),
+                   torch.empty((3,) + self.shape, dtype=u_host.dtype, pin_memory=True))
+        check(self._lib.lbm_init(self._h, _ptr(rho_host), _ptr(u_host), dt), self._h)
+        check(self._lib.lbm_step(self._h, int(nsteps)), self._h)
+        check(self._lib.lbm_moments(self._h, _ptr(out[0]), _ptr(out[1]), dt), self._h)
+        self.stream.synchronize()
         return out
 
     def close(self):
