@@ -129,6 +129,111 @@ __device__ __forceinline__ void adj_pair(const CellEq<R, false> &e, const R mu[Q
     cf += D * fraw[k];
 }
 
+// Double-float numbers: an unevaluated sum hi + lo of two floats.  Sums of
+// FP32 terms built with error-free transformations (TwoSum) keep about 48
+// bits, as many as FP64 sums of the same FP32 terms would, and run on the FP32
+// pipe.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = a.hi + b.hi;
+    const float bv = s - a.hi;
+    float e = (a.hi - (s - bv)) + (b.hi - bv);
+    e += a.lo + b.lo;
+    const float hi = s + e;
+    return DF{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DF b{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+        a = df_add(a, b);
+    }
+    return a;
+}
+
+// The adjoint of one cell: from the forward populations f of the state at t
+// (rho0 = 1) and mu = S^T lambda(t+1), the cell's lambda(t) (out) and its
+// terms of dL/domega+ (gp) and dL/domega- (gm).
+template <typename R>
+__device__ __forceinline__ void adjoint_cell(const R f[Q], const R mu[Q], const AdjConst<R> &p, R out[Q], R &gp,
+                                             R &gm)
+{
+    const CellEq<R, false> e(f, p.r);
+    // omega gradients of this cell:
+    //   sum_q mu+_q (f - feq)_q = mu0 (f0 - feq0) + 1/2 sum_k S_k (s - 2 sym)_k
+    //   sum_q mu-_q (f - feq)_q = 1/2 sum_k D_k (d - 2 asym)_k
+    R cgp = R(0), cgm = R(0), cf_ = R(0);
+    adj_pair<R, 0>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 1>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 2>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 3>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 4>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 5>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 6>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 7>(e, mu, p.fraw, cgp, cgm, cf_);
+    adj_pair<R, 8>(e, mu, p.fraw, cgp, cgm, cf_);
+    gp = -(mu[0] * (f[0] - e.eq0) + R(0.5) * cgp);
+    gm = R(-0.5) * (cgm + cf_);
+    // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
+    R Ssum_f = R(0), Ssum_e = R(0);
+    R face[3] = {R(0), R(0), R(0)}, edge[3] = {R(0), R(0), R(0)};
+    R Bd[3] = {R(0), R(0), R(0)};
+    R cxx = R(0), cyy = R(0), czz = R(0), cxy = R(0), cxz = R(0), cyz = R(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
+        const R w = WQ<R>(q);
+        if (NORM2(q) == 1) {
+            Ssum_f += S;
+            face[CX(q) ? 0 : (CY(q) ? 1 : 2)] += S;
+        } else {
+            Ssum_e += S;
+            edge[CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2)] += S;
+        }
+        const R wD = w * D, wS = w * S;
+        if (CX(q)) Bd[0] += R(CX(q)) * wD;
+        if (CY(q)) Bd[1] += R(CY(q)) * wD;
+        if (CZ(q)) Bd[2] += R(CZ(q)) * wD;
+        if (CX(q)) cxx += wS;
+        if (CY(q)) cyy += wS;
+        if (CZ(q)) czz += wS;
+        if (CX(q) * CY(q)) cxy += R(CX(q) * CY(q)) * wS;
+        if (CX(q) * CZ(q)) cxz += R(CX(q) * CZ(q)) * wS;
+        if (CY(q) * CZ(q)) cyz += R(CY(q) * CZ(q)) * wS;
+    }
+    const R wp = p.r.wp;
+    const R A = wp * (WQ<R>(0) * mu[0] + WQ<R>(1) * Ssum_f + WQ<R>(7) * Ssum_e);
+    const R *u = e.u;
+    const R cu3[3] = {cxx * u[0] + cxy * u[1] + cxz * u[2], cxy * u[0] + cyy * u[1] + cyz * u[2],
+                      cxz * u[0] + cyz * u[1] + czz * u[2]};
+    const R fs = face[0] + face[1] + face[2];
+    R G[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const R gs = R(3) * p.wm * Bd[i] + R(9) * wp * cu3[i] - R(3) * A * u[i];
+        const R gd = wp * (mu[0] * (R(1) / R(3)) - (fs - face[i]) * (R(1) / R(6)) + edge[i] * (R(1) / R(12)));
+        G[i] = gs + p.kappa * gd * u[i];
+    }
+    out[0] = (R(1) - wp) * mu[0] + A;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
+        const R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
+        const R t = A - p.r.hp * S;
+        const R hd = p.r.hm * D;
+        out[q] = mu[q] + t - hd + cg;
+        out[q + 1] = mu[q + 1] + t + hd - cg;
+    }
+}
+
 // Addressing as in the forward step kernels: plane base pointers from the
 // kernel parameters, nine wrapped row offsets per thread (Site), and no
 // bounce-back logic when the lattice is periodic (WALLS = false).
@@ -163,116 +268,119 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             const L *a = w ? lam_next.p[OPP(q)] + self : lam_next.p[q] + st.template row_along<1>(q) + xt;
             mu[q] = R(*a);
         }
-        const CellEq<R, false> e(f, p.r);
-        // omega gradients of this cell:
-        //   sum_q mu+_q (f - feq)_q = mu0 (f0 - feq0) + 1/2 sum_k S_k (s - 2 sym)_k
-        //   sum_q mu-_q (f - feq)_q = 1/2 sum_k D_k (d - 2 asym)_k
-        R cgp = R(0), cgm = R(0), cf_ = R(0);
-        adj_pair<R, 0>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 1>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 2>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 3>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 4>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 5>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 6>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 7>(e, mu, p.fraw, cgp, cgm, cf_);
-        adj_pair<R, 8>(e, mu, p.fraw, cgp, cgm, cf_);
-        gp_cell = -(mu[0] * (f[0] - e.eq0) + R(0.5) * cgp);
-        gm_cell = R(-0.5) * (cgm + cf_);
-        // lambda_p = mu_p - omega+ mu+_p - omega- mu-_p + A + c_p . G
-        R Ssum_f = R(0), Ssum_e = R(0);
-        R face[3] = {R(0), R(0), R(0)}, edge[3] = {R(0), R(0), R(0)};
-        R Bd[3] = {R(0), R(0), R(0)};
-        R cxx = R(0), cyy = R(0), czz = R(0), cxy = R(0), cxz = R(0), cyz = R(0);
+        R out[Q];
+        adjoint_cell(f, mu, p, out, gp_cell, gm_cell);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int q = 2 * k + 1;
-            const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
-            const R w = WQ<R>(q);
-            if (NORM2(q) == 1) {
-                Ssum_f += S;
-                face[CX(q) ? 0 : (CY(q) ? 1 : 2)] += S;
-            } else {
-                Ssum_e += S;
-                edge[CX(q) == 0 ? 0 : (CY(q) == 0 ? 1 : 2)] += S;
-            }
-            const R wD = w * D, wS = w * S;
-            if (CX(q)) Bd[0] += R(CX(q)) * wD;
-            if (CY(q)) Bd[1] += R(CY(q)) * wD;
-            if (CZ(q)) Bd[2] += R(CZ(q)) * wD;
-            if (CX(q)) cxx += wS;
-            if (CY(q)) cyy += wS;
-            if (CZ(q)) czz += wS;
-            if (CX(q) * CY(q)) cxy += R(CX(q) * CY(q)) * wS;
-            if (CX(q) * CZ(q)) cxz += R(CX(q) * CZ(q)) * wS;
-            if (CY(q) * CZ(q)) cyz += R(CY(q) * CZ(q)) * wS;
-        }
-        const R wp = p.r.wp;
-        const R A = wp * (WQ<R>(0) * mu[0] + WQ<R>(1) * Ssum_f + WQ<R>(7) * Ssum_e);
-        const R* u = e.u;
-        const R cu3[3] = {cxx * u[0] + cxy * u[1] + cxz * u[2], cxy * u[0] + cyy * u[1] + cyz * u[2],
-                          cxz * u[0] + cyz * u[1] + czz * u[2]};
-        const R fs = face[0] + face[1] + face[2];
-        R G[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const R gs = R(3) * p.wm * Bd[i] + R(9) * wp * cu3[i] - R(3) * A * u[i];
-            const R gd = wp * (mu[0] * (R(1) / R(3)) - (fs - face[i]) * (R(1) / R(6)) + edge[i] * (R(1) / R(12)));
-            G[i] = gs + p.kappa * gd * u[i];
-        }
-        lam.p[0][self] = L((R(1) - wp) * mu[0] + A);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int q = 2 * k + 1;
-            const R S = mu[q] + mu[q + 1], D = mu[q] - mu[q + 1];
-            const R cg = R(CX(q)) * G[0] + R(CY(q)) * G[1] + R(CZ(q)) * G[2];
-            const R t = A - p.r.hp * S;
-            const R hd = p.r.hm * D;
-            lam.p[q][self] = L(mu[q] + t - hd + cg);
-            lam.p[q + 1][self] = L(mu[q + 1] + t + hd - cg);
-        }
+        for (int q = 0; q < Q; ++q) lam.p[q][self] = L(out[q]);
     }
-    // Block partial in FP64: the per-cell terms are staged in shared memory (in
-    // the compute precision) and one warp accumulates them in double (fixed
-    // order), which keeps the FP64 instruction count per cell low on this GPU's
-    // FP64 pipe.
+    // Block partial: the per-cell terms are staged in shared memory (in the
+    // compute precision) and one warp sums them in a fixed order: in FP64 for
+    // FP64 storage, in double-float (see below) for the FP32 arithmetic.
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
     shp[tid] = gp_cell;
     shm[tid] = gm_cell;
     __syncthreads();
     if (tid < 32) {
-        double a0 = 0.0, a1 = 0.0;
-        for (int i = tid; i < nthreads; i += 32) {
-            a0 += (double)shp[i];
-            a1 += (double)shm[i];
-        }
+        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if constexpr (sizeof(R) == 8) {
+            double a0 = 0.0, a1 = 0.0;
+            for (int i = tid; i < nthreads; i += 32) {
+                a0 += (double)shp[i];
+                a1 += (double)shm[i];
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, o);
-            a1 += __shfl_down_sync(0xffffffffu, a1, o);
-        }
-        if (tid == 0) {
-            const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            partial[2 * b] = a0;
-            partial[2 * b + 1] = a1;
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_down_sync(0xffffffffu, a0, o);
+                a1 += __shfl_down_sync(0xffffffffu, a1, o);
+            }
+            if (tid == 0) reinterpret_cast<double2 *>(partial)[b] = make_double2(a0, a1);
+        } else {
+            DF a0{0.f, 0.f}, a1{0.f, 0.f};
+            for (int i = tid; i < nthreads; i += 32) {
+                two_sum_acc(a0.hi, a0.lo, (float)shp[i]);
+                two_sum_acc(a1.hi, a1.lo, (float)shm[i]);
+            }
+            a0 = df_warp_sum(a0);
+            a1 = df_warp_sum(a1);
+            if (tid == 0) reinterpret_cast<float4 *>(partial)[b] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_adjoint_final(const double *partial, long long nblocks, double *grad_omega)
+// Sum of the per-block partials of k_adjoint_step into grad_omega (fixed
+// order), one block of ADJ_FINAL_THREADS; each thread's loads are unrolled so
+// that they are in flight together.  FP64 partials (FP64 storage) are summed in
+// FP64; the double-float partials of the FP32 arithmetic in double-float, and
+// the result is added to grad_omega in FP64.  Summing the 8192 FP64 partials of
+// the 128^3 adjoint workload in FP64 on the one SM took 11 us, an eighth of
+// the step, because this GPU's FP64 pipe is narrow; double-float sums run on
+// the FP32 pipe.
+constexpr int ADJ_FINAL_THREADS = 1024;
+
+__global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final(const double2 *partial, long long nblocks,
+                                                                     double *grad_omega)
 {
     __shared__ double sh[32];
     double a0 = 0.0, a1 = 0.0;
-    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        a0 += partial[2 * b];
-        a1 += partial[2 * b + 1];
+    long long b = threadIdx.x;
+    for (; b + 7 * ADJ_FINAL_THREADS < nblocks; b += 8 * ADJ_FINAL_THREADS) {
+        double2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = partial[b + i * ADJ_FINAL_THREADS];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            a0 += v[i].x;
+            a1 += v[i].y;
+        }
+    }
+    for (; b < nblocks; b += ADJ_FINAL_THREADS) {
+        const double2 v = partial[b];
+        a0 += v.x;
+        a1 += v.y;
     }
     a0 = block_sum(a0, sh);
     a1 = block_sum(a1, sh);
     if (threadIdx.x == 0) {
         grad_omega[0] += a0;
         grad_omega[1] += a1;
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final_df(const float4 *partial, long long nblocks,
+                                                                        double *grad_omega)
+{
+    __shared__ float4 sh[ADJ_FINAL_THREADS / 32];
+    DF a0{0.f, 0.f}, a1{0.f, 0.f};
+    long long b = threadIdx.x;
+    for (; b + 7 * ADJ_FINAL_THREADS < nblocks; b += 8 * ADJ_FINAL_THREADS) {
+        float4 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = partial[b + i * ADJ_FINAL_THREADS];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            a0 = df_add(a0, DF{v[i].x, v[i].y});
+            a1 = df_add(a1, DF{v[i].z, v[i].w});
+        }
+    }
+    for (; b < nblocks; b += ADJ_FINAL_THREADS) {
+        const float4 v = partial[b];
+        a0 = df_add(a0, DF{v.x, v.y});
+        a1 = df_add(a1, DF{v.z, v.w});
+    }
+    a0 = df_warp_sum(a0);
+    a1 = df_warp_sum(a1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
+    __syncthreads();
+    if (warp == 0) {
+        const float4 v = lane < (int)(blockDim.x >> 5) ? sh[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        a0 = df_warp_sum(DF{v.x, v.y});
+        a1 = df_warp_sum(DF{v.z, v.w});
+        if (lane == 0) {
+            grad_omega[0] += (double)a0.hi + (double)a0.lo;
+            grad_omega[1] += (double)a1.hi + (double)a1.lo;
+        }
     }
 }
 
@@ -320,7 +428,12 @@ static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam
         k_adjoint_step<T, L, false><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, scratch, g, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_adjoint_final<<<1, 256, 0, s>>>(scratch, (long long)adjoint_blocks(g), grad_omega);
+    if (sizeof(R) == 8)
+        k_adjoint_final<<<1, ADJ_FINAL_THREADS, 0, s>>>(reinterpret_cast<const double2 *>(scratch),
+                                                        (long long)adjoint_blocks(g), grad_omega);
+    else
+        k_adjoint_final_df<<<1, ADJ_FINAL_THREADS, 0, s>>>(reinterpret_cast<const float4 *>(scratch),
+                                                           (long long)adjoint_blocks(g), grad_omega);
     return cudaGetLastError();
 }
 
