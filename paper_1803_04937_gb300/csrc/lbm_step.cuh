@@ -532,13 +532,12 @@ __device__ __forceinline__ void load4w(const Planes<T> &P, const Site<WALLS> &s,
         const uint2 *pn = reinterpret_cast<const uint2 *>(srcq + srow + (cx > 0 ? xprev : xnext));
         const bool xwall = WALLS && ((cx > 0 && s.bxm) || (cx < 0 && s.bxp));
         if (xwall && !w) pn = reinterpret_cast<const uint2 *>(bncq + s.own + xs);
-        if constexpr (!SWAP) {
-            win[q] = __ldg(pq);
-            if (cx != 0) nb[q] = w ? make_uint2(0u, 0u) : __ldg(pn);
-        } else {
-            win[q] = *pq;
-            if (cx != 0) nb[q] = w ? make_uint2(0u, 0u) : *pn;
-        }
+        // Non-coherent loads, also in the in-place AA odd step (SWAP): the
+        // elements it uses of a quad are its own cells' inputs, which only this
+        // thread writes, and only after it has read them; the other elements of
+        // a neighbour quad may be stale there and are not used.
+        win[q] = __ldg(pq);
+        if (cx != 0) nb[q] = w ? make_uint2(0u, 0u) : __ldg(pn);
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
