@@ -306,6 +306,9 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             if (tid == 0) reinterpret_cast<float4 *>(partial)[b] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
         }
     }
+    // the sum of the partials (launched as a programmatic dependent) may start
+    // once every block has got here; it waits for this grid's memory itself
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Sum of the per-block partials of k_adjoint_step into grad_omega (fixed
@@ -321,6 +324,7 @@ constexpr int ADJ_FINAL_THREADS = 1024;
 __global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final(const double2 *partial, long long nblocks,
                                                                      double *grad_omega)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // k_adjoint_step has finished, its partials visible
     __shared__ double sh[32];
     double a0 = 0.0, a1 = 0.0;
     long long b = threadIdx.x;
@@ -350,6 +354,7 @@ __global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final(const doubl
 __global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final_df(const float4 *partial, long long nblocks,
                                                                         double *grad_omega)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // k_adjoint_step has finished, its partials visible
     __shared__ float4 sh[ADJ_FINAL_THREADS / 32];
     DF a0{0.f, 0.f}, a1{0.f, 0.f};
     long long b = threadIdx.x;
@@ -428,12 +433,26 @@ static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam
         k_adjoint_step<T, L, false><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, scratch, g, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // The final sum is a programmatic dependent launch: it is scheduled while
+    // the step kernel's last blocks run (griddepcontrol.launch_dependents) and
+    // waits inside for the step's completion (griddepcontrol.wait), which hides
+    // the launch gap between the two.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, 1, 1);
+    cfg.blockDim = dim3(ADJ_FINAL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const long long nb = adjoint_blocks(g);
     if (sizeof(R) == 8)
-        k_adjoint_final<<<1, ADJ_FINAL_THREADS, 0, s>>>(reinterpret_cast<const double2 *>(scratch),
-                                                        (long long)adjoint_blocks(g), grad_omega);
+        e = cudaLaunchKernelEx(&cfg, k_adjoint_final, reinterpret_cast<const double2 *>(scratch), nb, grad_omega);
     else
-        k_adjoint_final_df<<<1, ADJ_FINAL_THREADS, 0, s>>>(reinterpret_cast<const float4 *>(scratch),
-                                                           (long long)adjoint_blocks(g), grad_omega);
+        e = cudaLaunchKernelEx(&cfg, k_adjoint_final_df, reinterpret_cast<const float4 *>(scratch), nb, grad_omega);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
