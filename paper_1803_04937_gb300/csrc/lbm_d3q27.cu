@@ -112,12 +112,32 @@ __device__ __forceinline__ void collide27(R g[Q27], const Relax27<R> &p)
         if (CY(q)) j[1] += R(CY(q)) * d[k];
         if (CZ(q)) j[2] += R(CZ(q)) * d[k];
     }
-    R P = R(1), u[3];
+    R P = R(1), u[3], du[3] = {R(0), R(0), R(0)};
+    constexpr bool COMP = compensated_v<R, ONE_ROUNDING> && !RHO0;
     if (RHO0) {
         P = R(1) + drho;
         const R inv = R(1) / P;
 #pragma unroll
         for (int i = 0; i < 3; ++i) u[i] = (j[i] + p.half_a[i]) * inv;
+    } else if (COMP) {
+        // compensated momentum, as CellEq does for D3Q19 (FP32 storage): u is
+        // rounded, du = (j + a/2) - u exactly, and the face pair of each axis
+        // (k = 0, 1, 2: c = +e_x, +e_y, +e_z) takes du out of its
+        // antisymmetric non-equilibrium, so the momentum balance stays exact
+        R hi[3] = {d[0], d[1], d[2]}, lo[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int k = 3; k < 13; ++k) {
+            const int q = 2 * k + 1;
+            if (CX(q) != 0) two_sum_acc(hi[0], lo[0], CX(q) > 0 ? d[k] : -d[k]);
+            if (CY(q) != 0) two_sum_acc(hi[1], lo[1], CY(q) > 0 ? d[k] : -d[k]);
+            if (CZ(q) != 0) two_sum_acc(hi[2], lo[2], CZ(q) > 0 ? d[k] : -d[k]);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            u[i] = hi[i];
+            two_sum_acc(u[i], lo[i], p.half_a[i]);
+            du[i] = lo[i];
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 3; ++i) u[i] = j[i] + p.half_a[i];
@@ -132,7 +152,8 @@ __device__ __forceinline__ void collide27(R g[Q27], const Relax27<R> &p)
         const R cu = R(CX(q)) * u[0] + R(CY(q)) * u[1] + R(CZ(q)) * u[2];
         const R sym = p.w[cls] * base + (P * p.K[cls]) * (cu * cu);
         const R nsym = fma(R(-2), sym, s[k]);
-        const R nasym = fma(-(P * p.A[cls]), cu, d[k]);
+        R nasym = fma(-(P * p.A[cls]), cu, d[k]);
+        if (COMP && k < 3) nasym -= du[k];
         const R b = fma(p.hm, nasym, -p.force[k]);
         if (ONE_ROUNDING) {
             g[q] = g[q] - fma(p.hp, nsym, b);

@@ -119,3 +119,34 @@ def test_d3q27_unsupported_calls_fail_cleanly():
     assert e.value.status == _lib.LBM_EUNSUPPORTED
     with pytest.raises(_lib.LBMError):
         Simulation(8, 8, 8, stencil=27, pattern="aa")
+
+
+def test_d3q27_channel_fp32_long_run():
+    """D3Q27, FP32: the walled channel of the benchmark workload (walls at
+    y = -1/2 and 255.5, TRT 3/16, tau = 0.6, body force for a centreline speed
+    of 0.05) on a thin 8x256x4 lattice, 5000 steps from rest: every (x, z)
+    column is bitwise equal and matches the FP64 oracle's D3Q27 1x256x1 column
+    to 1e-5.  This flow changes slowly, so without the compensated momentum sum
+    the FP32 rounding of u fed back through the relaxation every step would add
+    up coherently."""
+    from paper_1803_04937_gb300 import inputs
+    from paper_1803_04937_gb300.lbm import Simulation
+    nx, ny, nz, steps, tau = 8, 256, 4, 5000, 0.6
+    nu = (tau - 0.5) / 3
+    a = 8 * nu * 0.05 / ny ** 2
+    kw = dict(equilibrium="standard", collision="trt", tau=tau, force=(a, 0, 0), walls=(False, True, False))
+    sim = Simulation(nx, ny, nz, precision="f32", stencil=27, **kw)
+    rho, u = inputs.rest(nx, ny, nz, device="cuda")
+    sim.init(rho, u.float())
+    sim.step(steps)
+    _, ug = sim.moments(torch.float32)
+    ref = ug[:, 0:1, :, 0:1]
+    assert torch.equal(ug, ref.expand_as(ug)), "columns differ"
+    prof = ref[:, 0, :, 0].double().cpu().numpy()
+    sim.close()
+    cfg = oracle_config(1, ny, 1, stencil=27, **kw)
+    r1, u1 = inputs.rest(1, ny, 1)
+    _, uo = oracle.run(cfg, r1.numpy(), u1.numpy(), steps)
+    err = rel_maxnorm(prof[0], uo[0, 0, :, 0])
+    print("D3Q27 channel FP32, 5000 steps: u_x profile max-norm rel err vs FP64 oracle %.3e" % err)
+    assert err < 1e-5
