@@ -20,10 +20,10 @@ import oracle
 from tests._helpers import srt_collision_jacobian, srt_max_amplification
 
 
-def _oracle_collision_jacobian(eq, tau, U, h=1e-6):
+def _oracle_collision_jacobian(eq, tau, U, h=1e-6, collision=oracle.SRT, trt_magic=3 / 16):
     """Central differences of one oracle step on a 1x1x1 periodic lattice
     (streaming is the identity there, so the step is one collision)."""
-    cfg = oracle.Config(1, 1, 1, equilibrium=eq, collision=oracle.SRT, tau=tau)
+    cfg = oracle.Config(1, 1, 1, equilibrium=eq, collision=collision, tau=tau, trt_magic=trt_magic)
     feq = oracle.equilibrium(eq, np.ones((1, 1, 1)), np.asarray(U, dtype=np.float64).reshape(3, 1, 1, 1))
     feq = feq.reshape(19)
     J = np.zeros((19, 19))
@@ -91,3 +91,24 @@ def test_oracle_step_grows_at_the_predicted_rate():
     rate = (np.log(amp[oracle.IMPROVED][4]) - np.log(amp[oracle.IMPROVED][2])) / 400
     assert rate == pytest.approx(np.log(g), rel=0.03)
     assert amp[oracle.STANDARD][4] <= amp[oracle.STANDARD][0]
+
+
+def _max_amplification(J, c, n):
+    ks = 2 * np.pi * np.arange(n) / n
+    kk = np.stack(np.meshgrid(ks, ks, ks, indexing="ij"), axis=-1).reshape(-1, 3)
+    G = np.exp(-1j * (kk @ c.T.astype(np.float64)))[:, :, None] * J[None]
+    return float(np.abs(np.linalg.eigvals(G)).max())
+
+
+@pytest.mark.parametrize("magic", [1e-4, 3 / 16])
+def test_trt_does_not_stabilise_the_improved_equilibrium_at_tau_051(magic):
+    """TRT (Sec. 3.3) at tau = 0.51 with a small or the usual magic parameter,
+    linearised from the oracle's own collision: D3Q19-I still has a growing
+    mode at |U| = 0.1 along x, D3Q19-S none."""
+    for eq, grows in ((oracle.IMPROVED, True), (oracle.STANDARD, False)):
+        J, c = _oracle_collision_jacobian(eq, 0.51, (0.1, 0.0, 0.0), collision=oracle.TRT, trt_magic=magic)
+        g = _max_amplification(J, c, 16)
+        if grows:
+            assert g > 1.01
+        else:
+            assert g < 1 + 1e-6
