@@ -135,3 +135,37 @@ def test_hit_768_series():
     E, _, bad = _series(n, "f32", "improved", steps, 500, u_rms=0.01)
     print("HIT 768^3 improved FP32 at u_rms = 0.01: finite for %d steps (E %s)" % (steps, E))
     assert bad is None
+
+
+def test_uniform_flow_growth_rate_on_the_gpu():
+    """The GPU step (FP64) reproduces the linear instability behind the 768^3
+    blow-up: a uniform flow U = 0.1 e_x on a periodic 16^3 lattice with a
+    seeded 1e-9 velocity perturbation, SRT tau = 0.51, grows under D3Q19-I at
+    the largest amplification factor of the linearised step (within 3 %, steps
+    400 -> 800) and does not grow under D3Q19-S."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    from tests._helpers import srt_max_amplification
+    n, tau = 16, 0.51
+    rng = np.random.default_rng(5)
+    u = np.zeros((3, n, n, n))
+    u[0] = 0.1
+    u += 1e-9 * rng.standard_normal(u.shape)
+    amp = {}
+    for equilibrium in ("standard", "improved"):
+        sim = Simulation(n, n, n, equilibrium=equilibrium, collision="srt", tau=tau, precision="f64")
+        sim.init(None, torch.from_numpy(u).cuda())
+        a = []
+        for t in range(0, 801, 200):
+            if t:
+                sim.step(200)
+            _, ug = sim.moments()
+            ug[0] -= 0.1
+            a.append(float(ug.abs().max()))
+        sim.close()
+        amp[equilibrium] = a
+    g = srt_max_amplification((0.1, 0, 0), True, tau, n)
+    rate = (np.log(amp["improved"][4]) - np.log(amp["improved"][2])) / 400
+    print("uniform flow 16^3 tau 0.51: perturbation S %s, I %s; I growth rate %.5f per step, linear theory %.5f"
+          % (["%.1e" % x for x in amp["standard"]], ["%.1e" % x for x in amp["improved"]], rate, np.log(g)))
+    assert rate == pytest.approx(np.log(g), rel=0.03)
+    assert amp["standard"][4] <= amp["standard"][0]
