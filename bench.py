@@ -347,18 +347,21 @@ def adjoint_ratio(args, n=128, horizon=400):
             "ratio_backward_over_forward_pass": (t2 - t1) / (t1 - t0)}
 
 
-def e2e(args, n, calls=3, steps_per_call=(100, 2000)):
+def e2e(args, n, dist=None, device=None, calls=3, steps_per_call=(100, 2000)):
     """Same metric through the C ABI from pinned host buffers: each call is
     lbm_init reading rho, u from host memory, steps_per_call steps, and
     lbm_moments writing rho, u to host memory, then a stream synchronise (the
     host-device transfers are inside the timed region: the init and moments
     kernels read and write the pinned host buffers directly).  Reported for
     100 steps per call (the headline figure) and for the shear-wave
-    configuration's 2000 steps per call."""
+    configuration's 2000 steps per call.  Under torchrun every rank runs its
+    replica; barrier before, max-over-ranks time, all ranks' updates counted
+    (bytes per step are per rank)."""
     import torch
     from paper_1803_04937_gb300.lbm import Simulation
+    ws = dist.get_world_size() if dist else 1
     sim = Simulation(n, n, n, equilibrium=args.equilibrium, collision=args.collision, tau=args.tau,
-                     precision=args.precision, pattern=args.pattern)
+                     precision=args.precision, pattern=args.pattern, device=device or "cuda")
     dt = torch.float64 if args.precision == "f64" else torch.float32
     rho, u = shear_workload(n, n, n, "cpu")
     rho_h = rho.to(dt).pin_memory()
@@ -370,11 +373,13 @@ def e2e(args, n, calls=3, steps_per_call=(100, 2000)):
     for spc in steps_per_call:
         sim.run_host(rho_h, u_h, spc, out)  # warm-up (also captures the step graph)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(calls):
             sim.run_host(rho_h, u_h, spc, out)
-        t = time.perf_counter() - t0
-        res[spc] = {"value": n ** 3 * spc * calls / t / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi / spc,
+        t = max_over_ranks(time.perf_counter() - t0, dist, device)
+        res[spc] = {"value": ws * n ** 3 * spc * calls / t / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi / spc,
                     "d2h_bytes_per_step": bo / spc, "lbm_steps_per_call": spc, "h2d_bytes_per_call": bi,
                     "d2h_bytes_per_call": bo, "calls": calls}
     sim.close()
@@ -532,6 +537,8 @@ def run_native(args):
         "gpu_launches": args.steps,
         "clocks": sampler.summary(),
     }
+    if not args.no_extras and ws > 1:
+        line["e2e"] = e2e(args, n, dist, device)  # every rank takes part
     if rank == 0 and not args.no_extras and ws == 1:
         line["e2e"] = e2e(args, n)
         variants = {}
@@ -554,7 +561,7 @@ def run_native(args):
         line["variants"] = variants
         line["configs"] = config_variants(peak)
         line["adjoint"] = adjoint_ratio(args)
-    elif rank == 0:
+    elif rank == 0 and args.no_extras:
         line["e2e"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(12.0, single_thread_seconds=4.0)
