@@ -299,11 +299,12 @@ def test_duct_lambda_dependence():
     """Sec. 5.1, Fig. 1 right: the D3Q19-S spurious currents depend on
     Lambda^2 = (1/omega - 1/2)^2; the analysis (Sec. 4) puts the leading error
     term's zero at Lambda^2 = 1/12.  Measured at Re = 10: the minimum over
-    Lambda^2 moves towards 1/12 as D grows (higher-order terms shift it at
-    small D), and D3Q19-I stays at rounding level for every Lambda."""
+    Lambda^2 moves towards 1/12 as D grows from 16 to 32 to 64 (higher-order
+    terms shift it at small D), and D3Q19-I stays at rounding level for every
+    Lambda."""
     lam2 = [0.01, 0.03, 0.05, 0.0667, 1 / 12, 0.1, 0.12, 0.16, 0.25]
     argmin = {}
-    for D in (16, 32):
+    for D in (16, 32, 64):
         rs, ri = [], []
         for l2 in lam2:
             tau = 0.5 + math.sqrt(l2)
@@ -316,10 +317,11 @@ def test_duct_lambda_dependence():
         if D == 32:
             k = lam2.index(1 / 12)
             assert rs[k] < 0.2 * rs[-1] and rs[k] < 0.35 * rs[0]
-    print("duct: Lambda^2 of the smallest S current: D=16 %.4f, D=32 %.4f (analysis: %.4f)"
-          % (argmin[16], argmin[32], 1 / 12))
-    assert argmin[16] <= argmin[32] <= 0.1
+    print("duct: Lambda^2 of the smallest S current: D=16 %.4f, D=32 %.4f, D=64 %.4f (analysis: %.4f)"
+          % (argmin[16], argmin[32], argmin[64], 1 / 12))
+    assert argmin[16] <= argmin[32] <= argmin[64] <= 0.1
     assert argmin[32] >= 0.05
+    assert argmin[64] == 1 / 12  # measured: the grid point of the analysis' optimum
 
 
 def test_duct_convergence_orders():
