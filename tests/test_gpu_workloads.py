@@ -328,10 +328,10 @@ def test_duct_convergence_orders():
     """Sec. 5.1, Fig. 2: at Lambda^2 = 4/25 the D3Q19-S spurious-current ratio
     converges at second order under diffusive scaling (fixed tau, Re = 10)."""
     tau = 0.5 + 0.4
-    r = [_duct_ratio(D, tau, "standard") for D in (12, 24, 48)]
-    orders = [math.log2(r[i] / r[i + 1]) for i in range(2)]
+    r = [_duct_ratio(D, tau, "standard") for D in (12, 24, 48, 96)]
+    orders = [math.log2(r[i] / r[i + 1]) for i in range(3)]
     print("duct Lambda^2=4/25 S ratios %s, observed orders %s" % (r, orders))
-    assert 1.6 < orders[-1] < 2.4
+    assert 1.6 < orders[-2] < 2.4 and 1.8 < orders[-1] < 2.2
 
 
 def test_shear_wave_with_normal_velocity_profile():
