@@ -664,14 +664,14 @@ __global__ void __launch_bounds__(128, 5) k_aa_even4(Planes<T> P, Planes<T> Pw, 
 // quad goes to plane qbar of the own cells.  Each location is written by one
 // thread, and read (for a value that is used) only by that thread, as in the
 // one-cell kernel.
-template <typename T, bool RHO0, bool WALLS, bool MRT = false>
-__global__ void __launch_bounds__(128, MRT ? 4 : 5) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p)
+template <typename T, bool RHO0, bool WALLS, bool MRT = false, bool ROWS = false>
+__global__ void __launch_bounds__(128, MRT ? 4 : 5) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p, Rows r)
 {
     const int lane = threadIdx.x & 31;
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (y >= g.ny) return;  // uniform across the warp
+    const int y = (ROWS ? r.y0 : 0) + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    const int z = (ROWS ? r.z0 : 0) + (int)blockIdx.z;
+    if (y >= (ROWS ? r.y1 : g.ny)) return;  // uniform across the warp
     const bool active = x0 < g.nx;
     const Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
     const int xs = s.x;
@@ -790,6 +790,23 @@ static void launch_ab4(const Planes<T> &S, const Planes<T> &D, const Geo &g, con
     });
 }
 
+// The four-cell AA odd step, split into interior and wall rows as the A/B
+// step is (split_rows): the walled kernel spills and runs the walled channel
+// 512x256x256's odd step at 0.55 of the copy bandwidth (FP16 and BF16) as one
+// launch.  Each location is read and written by one cell's thread only, so
+// the launches may run in any order.
+template <typename T, bool RHO0, bool WALLS, bool MRT>
+static void launch_aa_odd4(const Planes<T> &P, const Geo &g, const Relax<float> &p, dim3 block4, cudaStream_t stream)
+{
+    split_rows<WALLS>(g, [&](bool walled, Rows r, int nzr) {
+        const dim3 grid((g.nx + 4 * block4.x - 1) / (4 * block4.x), (r.y1 - r.y0 + block4.y - 1) / block4.y, nzr);
+        if (walled)
+            k_aa_odd4<T, RHO0, true, MRT, WALLS><<<grid, block4, 0, stream>>>(P, g, p, r);
+        else
+            k_aa_odd4<T, RHO0, false, MRT, WALLS><<<grid, block4, 0, stream>>>(P, g, p, r);
+    });
+}
+
 template <typename T, bool RHO0, bool WALLS>
 static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const CollBoth &cb, LaunchShape ls,
                           cudaStream_t stream)
@@ -835,13 +852,13 @@ static cudaError_t step_t(int kind, void *src, void *dst, const Geo &g, const Co
                 else if (kind == 1)
                     k_aa_even4<T, RHO0, true><<<grid4, block4, 0, stream>>>(D, D, g, p);
                 else
-                    k_aa_odd4<T, RHO0, WALLS, true><<<grid4, block4, 0, stream>>>(D, g, p);
+                    launch_aa_odd4<T, RHO0, WALLS, true>(D, g, p, block4, stream);
             } else if (kind == 0) {
                 launch_ab4<T, RHO0, WALLS, false>(planes_of<T>(src, g.ncell), D, g, p, block4, stream);
             } else if (kind == 1) {
                 k_aa_even4<T, RHO0><<<grid4, block4, 0, stream>>>(D, D, g, p);
             } else {
-                k_aa_odd4<T, RHO0, WALLS><<<grid4, block4, 0, stream>>>(D, g, p);
+                launch_aa_odd4<T, RHO0, WALLS, false>(D, g, p, block4, stream);
             }
         }
         return cudaGetLastError();

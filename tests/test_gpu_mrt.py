@@ -94,11 +94,13 @@ def test_mrt_aa_equals_ab_bitwise(case, precision):
 @pytest.mark.parametrize("precision", ["f16s", "bf16s"])
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("case", [0, 2, 3, 4])
-@pytest.mark.parametrize("shape", [(3, 7, 4), (4, 9, 40), (3, 5, 388), (2, 3, 1040)])
+@pytest.mark.parametrize("shape", [(3, 7, 4), (4, 9, 40), (3, 8, 64), (2, 6, 256), (3, 5, 388), (2, 3, 600),
+                                   (1, 2, 1000), (2, 3, 1040)])
 def test_mrt_four_cells_is_bitwise(shape, case, pattern, precision):
     """16-bit storage with nx % 4 == 0 runs MRT in the four-cell kernels (A/B
     and AA); they equal the one-cell MRT kernel bit for bit (ragged warps,
-    row-end and multi-block rows, walls on every axis)."""
+    row-end and multi-block rows, blocks of 32 x 4, 64 x 2 and 128 x 1
+    threads, walls on every axis)."""
     from paper_1803_04937_gb300.lbm import Simulation
     kw = CASES[case]
     rho, u = random_fields(shape, seed=41)

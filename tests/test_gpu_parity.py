@@ -87,16 +87,24 @@ def test_aa_equals_ab_bitwise(nx, case, precision):
         assert torch.equal(ua, ub) and torch.equal(ra, rb)
 
 
+# (nz, ny, nx) for the four-cell AA steps, with the block the launcher picks
+# (the fewest idle lanes at a row's end): nx = 4 (one quad, its own periodic
+# neighbour), 40 (a ragged warp), 64 (blocks of 32 x 4 rows, half a warp
+# idle), 256 (64 x 2, whole rows), 388 (128 x 1, ragged), 600 (32 x 4, five
+# blocks per row), 1000 (128 x 1, two blocks per row) and 1040 (32 x 4, nine
+# blocks per row).
+AA4_SHAPES = [(3, 7, 4), (4, 9, 40), (3, 8, 64), (2, 6, 256), (3, 5, 388), (2, 3, 600), (1, 2, 1000), (2, 3, 1040)]
+
+
 @pytest.mark.parametrize("precision", ["f16s", "bf16s"])
-@pytest.mark.parametrize("case", [0, 3, 4, 5, 6])
-@pytest.mark.parametrize("shape", [(3, 7, 4), (4, 9, 40), (3, 5, 388), (2, 3, 1040)])
+@pytest.mark.parametrize("case", [0, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("shape", AA4_SHAPES)
 def test_aa_four_cells_is_bitwise(shape, case, precision):
     """The four-cell AA steps (16-bit storage) against the one-cell A/B step,
-    bit for bit, after even and odd step counts: nx = 4 (a row is one quad,
-    its own periodic neighbour), a ragged warp (40), interior and row-end warps
-    (388), several blocks per row with a partial last block (1040); walls on
-    x (cases 4, 5), y (3) and z (4, 5) exercise the scalar edge writes
-    through a wall."""
+    bit for bit, after even and odd step counts, over the row and block shapes
+    of AA4_SHAPES; walls on x (cases 4, 5) take the shuffle kernel's scalar
+    edge writes through a wall, walls on y (3, 7) and z (4, 5) the whole quad
+    into the own cells."""
     kw = CASES[case]
     rho, u = random_fields(shape, seed=13)
     for steps in (1, 2, 5):
@@ -105,23 +113,24 @@ def test_aa_four_cells_is_bitwise(shape, case, precision):
         assert torch.equal(sa.get_pdfs(), sb.get_pdfs())
 
 
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("collision", ["trt", "mrt"])
 @pytest.mark.parametrize("precision", ["f16s", "bf16s"])
 @pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True)])
 @pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (6, 3, 1040)])
-def test_four_cell_ab_split_rows_is_bitwise(shape, walls, precision, collision):
-    """With walls on y and/or z only, the four-cell A/B step runs its interior
-    rows through the periodic kernel and the wall rows through the walled one
-    (split_rows), for the TRT and the MRT collision; the result is bitwise that
-    of the one-cell step, also on lattices of one or two rows or planes, which
-    have no interior."""
+def test_four_cell_split_rows_is_bitwise(shape, walls, precision, collision, pattern):
+    """With walls on y and/or z only, the four-cell A/B step and the AA odd
+    step run their interior rows through the periodic kernel and the wall rows
+    through the walled one (split_rows), for the TRT and the MRT collision; the
+    result is bitwise that of the one-cell A/B step, also on lattices of one or
+    two rows or planes, which have no interior."""
     kw = dict(equilibrium="improved", collision=collision, tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
     if collision == "mrt":
         kw.update(omega_bulk=1.3, omega_4=0.9)
     rho, u = random_fields(shape, seed=11)
-    for steps in (1, 5):
+    for steps in (1, 2, 5):
         sa, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=1)
-        sb, _, _ = _run_gpu(shape, rho, u, steps, precision, "ab", kw, cells_x=4)
+        sb, _, _ = _run_gpu(shape, rho, u, steps, precision, pattern, kw, cells_x=4)
         assert torch.equal(sa.get_pdfs(), sb.get_pdfs()), steps
 
 
