@@ -61,6 +61,27 @@ def test_d3q27_four_cells_is_bitwise(shape, case, precision):
     assert torch.equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("precision", ["f16s", "bf16s"])
+@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True)])
+@pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (6, 3, 1040)])
+def test_d3q27_four_cell_split_rows_is_bitwise(shape, walls, precision):
+    """With walls on y and/or z only, the four-cell D3Q27 step runs its
+    interior rows through the periodic kernel and the wall rows through the
+    walled one (split_rows); the result is bitwise that of the one-cell
+    kernel, also on lattices of one or two rows or planes (no interior)."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    kw = dict(collision="trt", tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
+    rho, u = random_fields(shape, seed=47)
+    nz, ny, nx = shape
+    out = []
+    for cells_x in (4, 1):
+        sim = Simulation(nx, ny, nz, precision=precision, stencil=27, equilibrium="standard", cells_x=cells_x, **kw)
+        sim.init(rho.cuda(), u.float().cuda())
+        sim.step(5)
+        out.append(sim.get_pdfs())
+    assert torch.equal(out[0], out[1])
+
+
 @pytest.mark.parametrize("precision,tol", [("f16s", 2e-3), ("bf16s", 2e-2)])
 def test_d3q27_16bit_storage_error(precision, tol):
     from paper_1803_04937_gb300.lbm import Simulation
