@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k27_ab1(const T *__restrict__ src, T *__r
 // formed by funnel shifts from the aligned quad and its aligned neighbour),
 // 27 populations.  Bitwise the same results as k27_ab1.  ROWS: only the rows
 // y in [r.y0, r.y1), z in [r.z0, r.z0 + gridDim.z) (split_rows).
-template <typename T, bool RHO0, bool WALLS, bool ROWS = false>
+template <typename T, bool RHO0, bool WALLS, bool ROWS = false, bool XONLY = false>
 __global__ void __launch_bounds__(128, 4) k27_ab4(const T *__restrict__ src, T *__restrict__ dst, Geo g,
                                                   Relax27<float> p, Rows r)
 {
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(128, 4) k27_ab4(const T *__restrict__ src, T *
     const int y = (ROWS ? r.y0 : 0) + (int)(blockIdx.y * blockDim.y + threadIdx.y);
     const int z = (ROWS ? r.z0 : 0) + (int)blockIdx.z;
     if (y >= (ROWS ? r.y1 : g.ny) || x0 >= g.nx) return;
-    const Site<WALLS> s(x0, y, z, 4, g);
+    Site<WALLS> s(x0, y, z, 4, g);
+    drop_yz<XONLY>(s);
     const int xprev = x0 == 0 ? g.nx - 4 : x0 - 4;
     const int xnext = x0 + 4 >= g.nx ? 0 : x0 + 4;
     const unsigned short *base = reinterpret_cast<const unsigned short *>(src);
@@ -445,9 +446,10 @@ cudaError_t launch_step27(int prec, const void *src, void *dst, const Geo &g, co
                     }
                 }
                 const dim3 bl4(bx, 128 / bx, 1);
-                // with walls on y and/or z only, the interior rows run the periodic
-                // kernel and the wall rows the walled one (split_rows): walled channel
-                // 512x256x256, FP16, 0.68 -> 1.0 of the copy bandwidth
+                // with walls, the interior rows run the periodic kernel (or with walls
+                // on x the x-walls-only one) and the wall rows the walled one
+                // (split_rows): walled channel 512x256x256, FP16, 0.68 -> 1.0 of the
+                // copy bandwidth
                 auto run = [&](auto rho0) {
                     constexpr bool RH = decltype(rho0)::value;
                     if (!walls) {
@@ -455,10 +457,12 @@ cudaError_t launch_step27(int prec, const void *src, void *dst, const Geo &g, co
                         q27::k27_ab4<T, RH, false><<<gr4, bl4, 0, stream>>>(a, b, g, p, Rows{0, g.ny, 0});
                         return;
                     }
-                    split_rows<true>(g, [&](bool walled, Rows r, int nzr) {
+                    split_rows<true>(g, [&](int kind, Rows r, int nzr) {
                         const dim3 gr4((g.nx + 4 * bx - 1) / (4 * bx), (r.y1 - r.y0 + bl4.y - 1) / bl4.y, nzr);
-                        if (walled)
+                        if (kind == ROWS_WALLED)
                             q27::k27_ab4<T, RH, true, true><<<gr4, bl4, 0, stream>>>(a, b, g, p, r);
+                        else if (kind == ROWS_XWALLS)
+                            q27::k27_ab4<T, RH, true, true, true><<<gr4, bl4, 0, stream>>>(a, b, g, p, r);
                         else
                             q27::k27_ab4<T, RH, false, true><<<gr4, bl4, 0, stream>>>(a, b, g, p, r);
                     });

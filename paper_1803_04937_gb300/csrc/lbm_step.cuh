@@ -113,6 +113,14 @@ struct Site {
     }
 };
 
+// Rows that touch no y/z wall on a lattice with walls on x (XONLY kernels):
+// the y/z wall flags are constant false, so only the x-wall selects remain.
+template <bool XONLY, bool WALLS>
+__device__ __forceinline__ void drop_yz(Site<WALLS> &s)
+{
+    if constexpr (XONLY) s.bym = s.byp = s.bzm = s.bzp = false;
+}
+
 // An in-place step writes the locations it has read; left alone, the compiler
 // keeps the 19 load addresses (64-bit each) alive through the collisions to
 // reuse them for the stores, and spills.  Passing the offsets through an
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(256, aa1_blocks<T, MRT>(false)) k_aa_even1(Pla
 // AA odd step: read plane qbar at x - c_q, write plane q at x + c_q (through
 // a wall: read plane q / write plane qbar of the own cell).  Every location is
 // read and written by exactly one thread.
-template <typename T, bool RHO0, bool WALLS, bool MRT = false, bool ROWS = false>
+template <typename T, bool RHO0, bool WALLS, bool MRT = false, bool ROWS = false, bool XONLY = false>
 __global__ void __launch_bounds__(256, aa1_blocks<T, MRT>(true)) k_aa_odd1(Planes<T> P, Geo g,
                                                                          Relax<typename Storage<T>::R> p, Rows r)
 {
@@ -290,7 +298,8 @@ __global__ void __launch_bounds__(256, aa1_blocks<T, MRT>(true)) k_aa_odd1(Plane
     const int y = (ROWS ? r.y0 : 0) + (int)(blockIdx.y * blockDim.y + threadIdx.y);
     const int z = (ROWS ? r.z0 : 0) + (int)blockIdx.z;
     if (x >= g.nx || y >= (ROWS ? r.y1 : g.ny)) return;
-    const Site<WALLS> s(x, y, z, 1, g);
+    Site<WALLS> s(x, y, z, 1, g);
+    drop_yz<XONLY>(s);
     R f[Q];
     gather1<true>(P, s, f);
     collide_any<R, RHO0, MRT, one_rounding_v<T>>(f, p);
@@ -607,14 +616,23 @@ __device__ __forceinline__ void ab4_body(const Planes<T> &src, const Planes<T> &
 template <typename T, bool WALLS>
 constexpr int ab4_blocks = (WALLS && std::is_same_v<T, __half>) ? 4 : 5;
 
-template <typename T, bool RHO0, bool WALLS, bool MRT = false>
-__global__ void __launch_bounds__(128, ab4_blocks<T, WALLS>) k_ab4(Planes<T> src, Planes<T> dst, Geo g,
-                                                                    Relax<float> p, Rows r)
+// XONLY: rows that touch no y/z wall on a lattice with walls on x (a
+// cavity's interior rows): one body with the x-wall selects only, which cost
+// little (the end quads' shifted windows take the reflected own quad).
+template <typename T, bool RHO0, bool WALLS, bool MRT = false, bool XONLY = false>
+__global__ void __launch_bounds__(128, ab4_blocks<T, WALLS && !XONLY>) k_ab4(Planes<T> src, Planes<T> dst, Geo g,
+                                                                              Relax<float> p, Rows r)
 {
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = r.y0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
     const int z = r.z0 + (int)blockIdx.z;
     if (y >= r.y1 || x0 >= g.nx) return;  // no lane needs another lane's data
+    if constexpr (XONLY) {
+        Site<true> sx(x0, y, z, 4, g);
+        drop_yz<true>(sx);
+        ab4_body<T, RHO0, true, MRT>(src, dst, sx, g, p);
+        return;
+    }
     if constexpr (WALLS) {
         // A warp covers one row segment; where none of its cells touches a wall
         // (all but the wall rows and the row ends) it takes the periodic body,
@@ -664,7 +682,7 @@ __global__ void __launch_bounds__(128, 5) k_aa_even4(Planes<T> P, Planes<T> Pw, 
 // quad goes to plane qbar of the own cells.  Each location is written by one
 // thread, and read (for a value that is used) only by that thread, as in the
 // one-cell kernel.
-template <typename T, bool RHO0, bool WALLS, bool MRT = false, bool ROWS = false>
+template <typename T, bool RHO0, bool WALLS, bool MRT = false, bool ROWS = false, bool XONLY = false>
 __global__ void __launch_bounds__(128, MRT ? 4 : 5) k_aa_odd4(Planes<T> P, Geo g, Relax<float> p, Rows r)
 {
     const int lane = threadIdx.x & 31;
@@ -673,7 +691,8 @@ __global__ void __launch_bounds__(128, MRT ? 4 : 5) k_aa_odd4(Planes<T> P, Geo g
     const int z = (ROWS ? r.z0 : 0) + (int)blockIdx.z;
     if (y >= (ROWS ? r.y1 : g.ny)) return;  // uniform across the warp
     const bool active = x0 < g.nx;
-    const Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
+    Site<WALLS> s(active ? x0 : 0, y, z, 4, g);
+    drop_yz<XONLY>(s);
     const int xs = s.x;
     const bool last = lane == 31 || xs + 4 >= g.nx;
     uint2 quad[Q];
@@ -736,33 +755,39 @@ __global__ void __launch_bounds__(128, MRT ? 4 : 5) k_aa_odd4(Planes<T> P, Geo g
 
 // ---------------------------------------------------------------- dispatch
 
-// Calls launch(walled, rows, nz_rows) for the launches of one four-cell A/B
-// step.  A periodic lattice, or one with walls on x, is one launch over all
-// rows.  With walls on y and/or z only, the interior rows (no link crosses a
-// wall) run the periodic kernel and the wall rows the walled one: rows y = 0
-// and ny - 1 over all z, then planes z = 0 and nz - 1 over the interior y;
-// every row is in exactly one launch.  Both kernels compute a cell with the
-// same code as the single walled launch, so the results are bitwise the same.
-// The walled four-cell kernel carries both bodies and spills; keeping it to
-// the wall rows took the walled channel 512x256x256 from 84.3 to 89.1 GLUPS
-// (FP16) and from 80.0 to 86.9 (BF16).
+// Calls launch(kind, rows, nz_rows) for the launches of one step.  A periodic
+// lattice is one ROWS_PERIODIC launch over all rows.  With walls, the interior
+// rows (no link crosses a y or z wall) run the periodic kernel, or with walls
+// on x the kernel that has the x-wall selects only (ROWS_XWALLS), and the wall
+// rows the walled one (ROWS_WALLED): rows y = 0 and ny - 1 over all z, then
+// planes z = 0 and nz - 1 over the interior y; every row is in exactly one
+// launch.  All kernels compute a cell with the same code as the single walled
+// launch, so the results are bitwise the same.  The walled four-cell kernel
+// carries both bodies and spills; keeping it to the wall rows took the walled
+// channel 512x256x256 from 84.3 to 89.1 GLUPS (FP16) and from 80.0 to 86.9
+// (BF16), and a cavity (walls on x, y and z) 512x256x256 from 0.76 to 0.95 of
+// the copy bandwidth (FP16 A/B).
+// Kinds of the launches of split_rows.
+enum { ROWS_PERIODIC = 0, ROWS_WALLED = 1, ROWS_XWALLS = 2 };
+
 template <bool WALLS, typename F>
 static void split_rows(const Geo &g, F &&launch)
 {
-    if (!WALLS || g.wall_x) {
-        launch(WALLS, Rows{0, g.ny, 0}, g.nz);
+    if (!WALLS) {
+        launch(ROWS_PERIODIC, Rows{0, g.ny, 0}, g.nz);
         return;
     }
+    const int inner = g.wall_x ? ROWS_XWALLS : ROWS_PERIODIC;
     const int ylo = g.wall_y ? 1 : 0, yhi = g.wall_y ? g.ny - 1 : g.ny;
     const int zlo = g.wall_z ? 1 : 0, zhi = g.wall_z ? g.nz - 1 : g.nz;
-    if (yhi > ylo && zhi > zlo) launch(false, Rows{ylo, yhi, zlo}, zhi - zlo);
+    if (yhi > ylo && zhi > zlo) launch(inner, Rows{ylo, yhi, zlo}, zhi - zlo);
     if (g.wall_y) {
-        launch(true, Rows{0, 1, 0}, g.nz);
-        if (g.ny > 1) launch(true, Rows{g.ny - 1, g.ny, 0}, g.nz);
+        launch(ROWS_WALLED, Rows{0, 1, 0}, g.nz);
+        if (g.ny > 1) launch(ROWS_WALLED, Rows{g.ny - 1, g.ny, 0}, g.nz);
     }
     if (g.wall_z && yhi > ylo) {
-        launch(true, Rows{ylo, yhi, 0}, 1);
-        if (g.nz > 1) launch(true, Rows{ylo, yhi, g.nz - 1}, 1);
+        launch(ROWS_WALLED, Rows{ylo, yhi, 0}, 1);
+        if (g.nz > 1) launch(ROWS_WALLED, Rows{ylo, yhi, g.nz - 1}, 1);
     }
 }
 
@@ -784,10 +809,12 @@ template <typename T, bool RHO0, bool WALLS, bool MRT>
 static void launch_aa_odd1(const Planes<T> &P, const Geo &g, const Relax<typename Storage<T>::R> &p, dim3 block,
                            cudaStream_t stream)
 {
-    split_rows<WALLS>(g, [&](bool walled, Rows r, int nzr) {
+    split_rows<WALLS>(g, [&](int kind, Rows r, int nzr) {
         const dim3 grid((g.nx + block.x - 1) / block.x, (r.y1 - r.y0 + block.y - 1) / block.y, nzr);
-        if (walled)
+        if (kind == ROWS_WALLED)
             k_aa_odd1<T, RHO0, true, MRT, WALLS><<<grid, block, 0, stream>>>(P, g, p, r);
+        else if (kind == ROWS_XWALLS)
+            k_aa_odd1<T, RHO0, true, MRT, true, true><<<grid, block, 0, stream>>>(P, g, p, r);
         else
             k_aa_odd1<T, RHO0, false, MRT, WALLS><<<grid, block, 0, stream>>>(P, g, p, r);
     });
@@ -797,10 +824,12 @@ template <typename T, bool RHO0, bool WALLS, bool MRT>
 static void launch_ab4(const Planes<T> &S, const Planes<T> &D, const Geo &g, const Relax<float> &p, dim3 block4,
                        cudaStream_t stream)
 {
-    split_rows<WALLS>(g, [&](bool walled, Rows r, int nzr) {
+    split_rows<WALLS>(g, [&](int kind, Rows r, int nzr) {
         const dim3 grid((g.nx + 4 * block4.x - 1) / (4 * block4.x), (r.y1 - r.y0 + block4.y - 1) / block4.y, nzr);
-        if (walled)
+        if (kind == ROWS_WALLED)
             k_ab4<T, RHO0, true, MRT><<<grid, block4, 0, stream>>>(S, D, g, p, r);
+        else if (kind == ROWS_XWALLS)
+            k_ab4<T, RHO0, true, MRT, true><<<grid, block4, 0, stream>>>(S, D, g, p, r);
         else
             k_ab4<T, RHO0, false, MRT><<<grid, block4, 0, stream>>>(S, D, g, p, r);
     });
@@ -814,10 +843,12 @@ static void launch_ab4(const Planes<T> &S, const Planes<T> &D, const Geo &g, con
 template <typename T, bool RHO0, bool WALLS, bool MRT>
 static void launch_aa_odd4(const Planes<T> &P, const Geo &g, const Relax<float> &p, dim3 block4, cudaStream_t stream)
 {
-    split_rows<WALLS>(g, [&](bool walled, Rows r, int nzr) {
+    split_rows<WALLS>(g, [&](int kind, Rows r, int nzr) {
         const dim3 grid((g.nx + 4 * block4.x - 1) / (4 * block4.x), (r.y1 - r.y0 + block4.y - 1) / block4.y, nzr);
-        if (walled)
+        if (kind == ROWS_WALLED)
             k_aa_odd4<T, RHO0, true, MRT, WALLS><<<grid, block4, 0, stream>>>(P, g, p, r);
+        else if (kind == ROWS_XWALLS)
+            k_aa_odd4<T, RHO0, true, MRT, true, true><<<grid, block4, 0, stream>>>(P, g, p, r);
         else
             k_aa_odd4<T, RHO0, false, MRT, WALLS><<<grid, block4, 0, stream>>>(P, g, p, r);
     });

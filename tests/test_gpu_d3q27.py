@@ -62,13 +62,15 @@ def test_d3q27_four_cells_is_bitwise(shape, case, precision):
 
 
 @pytest.mark.parametrize("precision", ["f16s", "bf16s"])
-@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True)])
-@pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (6, 3, 1040)])
+@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True), (True, False, False),
+                                   (True, True, True)])
+@pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (3, 2, 4), (6, 3, 1040)])
 def test_d3q27_four_cell_split_rows_is_bitwise(shape, walls, precision):
-    """With walls on y and/or z only, the four-cell D3Q27 step runs its
-    interior rows through the periodic kernel and the wall rows through the
-    walled one (split_rows); the result is bitwise that of the one-cell
-    kernel, also on lattices of one or two rows or planes (no interior)."""
+    """On a walled lattice the four-cell D3Q27 step runs its interior rows
+    through the periodic kernel (with walls on x, the kernel with the x-wall
+    selects only) and the wall rows through the walled one (split_rows); the
+    result is bitwise that of the one-cell kernel, also on lattices of one or
+    two rows or planes (no interior)."""
     from paper_1803_04937_gb300.lbm import Simulation
     kw = dict(collision="trt", tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
     rho, u = random_fields(shape, seed=47)

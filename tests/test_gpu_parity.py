@@ -116,14 +116,17 @@ def test_aa_four_cells_is_bitwise(shape, case, precision):
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("collision", ["trt", "mrt"])
 @pytest.mark.parametrize("precision", ["f16s", "bf16s"])
-@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True)])
-@pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (6, 3, 1040)])
+@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True), (True, False, False),
+                                   (True, True, True)])
+@pytest.mark.parametrize("shape", [(5, 7, 40), (1, 2, 388), (2, 1, 64), (2, 2, 8), (3, 2, 4), (6, 3, 1040)])
 def test_four_cell_split_rows_is_bitwise(shape, walls, precision, collision, pattern):
     """With walls on y and/or z only, the four-cell A/B step and the AA odd
     step run their interior rows through the periodic kernel and the wall rows
-    through the walled one (split_rows), for the TRT and the MRT collision; the
-    result is bitwise that of the one-cell A/B step, also on lattices of one or
-    two rows or planes, which have no interior."""
+    through the walled one (split_rows); with walls on x as well, the A/B step
+    runs the rows that touch no y/z wall through a kernel with the x-wall
+    selects only.  For the TRT and the MRT collision the result is bitwise that
+    of the one-cell A/B step, also on lattices of one or two rows or planes,
+    which have no interior."""
     kw = dict(equilibrium="improved", collision=collision, tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
     if collision == "mrt":
         kw.update(omega_bulk=1.3, omega_4=0.9)
@@ -135,13 +138,15 @@ def test_four_cell_split_rows_is_bitwise(shape, walls, precision, collision, pat
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True)])
+@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (False, True, True), (True, False, False),
+                                   (True, True, True)])
 @pytest.mark.parametrize("shape", [(5, 7, 37), (1, 2, 64), (2, 1, 45), (6, 3, 130)])
 def test_one_cell_aa_split_rows_is_bitwise(shape, walls, precision):
-    """The one-cell AA odd step on a lattice with walls on y and/or z only runs
-    its interior rows through the periodic kernel and the wall rows through the
-    walled one (split_rows); after even and odd step counts the populations are
-    bitwise those of the one-cell A/B step."""
+    """The one-cell AA odd step on a walled lattice runs its interior rows
+    through the periodic kernel (with walls on x, the kernel with the x-wall
+    selects only) and the wall rows through the walled one (split_rows); after
+    even and odd step counts the populations are bitwise those of the one-cell
+    A/B step."""
     kw = dict(equilibrium="improved", collision="trt", tau=0.6, walls=walls, force=(1e-4, -2e-4, 1e-4))
     rho, u = random_fields(shape, seed=23)
     for steps in (1, 2, 5):
