@@ -845,12 +845,16 @@ static void launch_aa_odd4(const Planes<T> &P, const Geo &g, const Relax<float> 
 {
     split_rows<WALLS>(g, [&](int kind, Rows r, int nzr) {
         const dim3 grid((g.nx + 4 * block4.x - 1) / (4 * block4.x), (r.y1 - r.y0 + block4.y - 1) / block4.y, nzr);
+        // the interior rows of a walled lattice take the x-walls-only kernel also
+        // without x walls (its x flags are then false): it compiles to a faster
+        // step than the periodic kernel with a row range (walled channel, FP16 AA
+        // pair 0.81 -> 0.85, BF16 0.80 -> 0.82)
         if (kind == ROWS_WALLED)
             k_aa_odd4<T, RHO0, true, MRT, WALLS><<<grid, block4, 0, stream>>>(P, g, p, r);
-        else if (kind == ROWS_XWALLS)
+        else if (WALLS)
             k_aa_odd4<T, RHO0, true, MRT, true, true><<<grid, block4, 0, stream>>>(P, g, p, r);
         else
-            k_aa_odd4<T, RHO0, false, MRT, WALLS><<<grid, block4, 0, stream>>>(P, g, p, r);
+            k_aa_odd4<T, RHO0, false, MRT><<<grid, block4, 0, stream>>>(P, g, p, r);
     });
 }
 
