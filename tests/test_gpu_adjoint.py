@@ -32,7 +32,7 @@ def _gpu_grad(shape, rho, u0, tgt, steps, precision, case, every=None):
                              checkpoint_every=every, **kw)
     L = 0.5 * ((uT.double() - tgt.to("cuda")) ** 2).sum()
     L.backward()
-    return float(L), u.grad.double().cpu().numpy(), float(tau.grad)
+    return L.item(), u.grad.double().cpu().numpy(), tau.grad.item()
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-4)])
