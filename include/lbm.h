@@ -48,7 +48,7 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_EINVAL        1  /* bad argument (null pointer, size, key, value) */
 #define LBM_ENOMEM        2  /* host allocation of the handle failed */
 #define LBM_ECUDA         3  /* a CUDA runtime call or kernel launch failed */
-#define LBM_EUNSUPPORTED  4  /* valid request this build does not implement */
+#define LBM_EUNSUPPORTED  4  /* valid request the library does not implement */
 #define LBM_ENONFINITE    5  /* lbm_reduce found NaN or Inf in the state */
 #define LBM_ESTATE        6  /* call out of order (e.g. lbm_step before lbm_bind) */
 
