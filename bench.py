@@ -313,8 +313,11 @@ def adjoint_ratio(args, n=128, horizon=400):
     state = ctypes.c_void_p(sim.grids[0].data_ptr())  # any A/B grid is a valid state for timing
     lp = [ctypes.c_void_p(t.data_ptr()) for t in lam]
     s = sim.stream
+    # deferred dL/domega sums, as the autograd backward runs them (flushed inside the timed region)
+    _lib.check(lib.lbm_set_option(sim.handle, _lib.OPT_ADJ_DEFER_SUM, 1.0), sim.handle)
     for i in range(10):
         _lib.check(lib.lbm_adjoint_step(sim.handle, state, lp[i % 2], lp[1 - i % 2], gwp), sim.handle)
+    _lib.check(lib.lbm_adjoint_flush(sim.handle), sim.handle)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -322,6 +325,7 @@ def adjoint_ratio(args, n=128, horizon=400):
     e0.record(s)
     for i in range(reps):
         lib.lbm_adjoint_step(sim.handle, state, lp[i % 2], lp[1 - i % 2], gwp)
+    lib.lbm_adjoint_flush(sim.handle)
     e1.record(s)
     torch.cuda.synchronize()
     t_adj = e0.elapsed_time(e1) * 1e-3 / reps

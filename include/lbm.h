@@ -120,6 +120,14 @@ typedef struct lbm_ctx *lbm_handle;
                                  by lbm_set_option and lbm_bind; not used while the bound stream
                                  is being captured by the caller); 0: one launch per step.
                                  Same results either way. */
+#define LBM_OPT_ADJ_DEFER_SUM 19  /* 0 (default): each lbm_adjoint_step adds its dL/domega
+                                 terms to its grad_omega before the call's work ends; 1:
+                                 the terms of a step are summed by the next lbm_adjoint_step
+                                 (in the first block of its kernel) or by lbm_adjoint_flush,
+                                 which takes a one-block kernel off each step's critical path.
+                                 Bitwise the same sums either way.  Changing the option,
+                                 lbm_bind, lbm_reduce, lbm_enstrophy and lbm_adjoint_seed
+                                 flush first; lbm_destroy drops a pending sum. */
 
 /* lbm_reduce output slots */
 #define LBM_RED_MASS      0   /* sum_x rho */
@@ -174,8 +182,9 @@ int lbm_get_option(lbm_handle h, int key, double *value);
  * Device memory the caller must provide:
  *   *pdf_bytes_per_grid  bytes of one PDF grid (19 * cells * element size)
  *   *n_grids             2 for LBM_PATTERN_AB, 1 for LBM_PATTERN_AA
- *   *scratch_bytes       bytes of the scratch buffer used by lbm_reduce and
- *                        lbm_adjoint_step (FP64 block partials)
+ *   *scratch_bytes       bytes of the scratch buffer used by lbm_reduce,
+ *                        lbm_enstrophy and lbm_adjoint_step (FP64 block partials;
+ *                        two buffers of adjoint partials for deferred sums)
  * Any pointer may be NULL.  Host only.
  */
 int lbm_required_bytes(lbm_handle h, size_t *pdf_bytes_per_grid, int *n_grids,
@@ -300,6 +309,12 @@ int lbm_set_pdfs(lbm_handle h, const void *src);
  *   the A/B layout exactly as the forward pass left it in the current grid
  *   (lbm_bind + lbm_step with LBM_PATTERN_AB), i.e. a checkpoint copy of it.
  *   lambda_next and lambda_t must not overlap.  Needs a bound scratch buffer.
+ *   With LBM_OPT_ADJ_DEFER_SUM = 1 the step's contributions reach grad_omega
+ *   only when the next lbm_adjoint_step's kernel or lbm_adjoint_flush has run
+ *   on the stream (the block partials wait in the scratch buffer).
+ *
+ * lbm_adjoint_flush: adds the contributions of a deferred step (if any) to its
+ *   grad_omega; enqueued on the bound stream.
  *
  * lbm_adjoint_init_velocity: dL/du0 from lambda(0) through f(0) =
  *   f^eq(rho, u0) (lbm_init).  rho may be NULL (rho = 1); grad_u0 has dtype.
@@ -315,6 +330,7 @@ int lbm_adjoint_seed(lbm_handle h, const void *grad_rho, const void *grad_u, int
                      void *lambda);
 int lbm_adjoint_step(lbm_handle h, const void *state_t, const void *lambda_next,
                      void *lambda_t, double *grad_omega);
+int lbm_adjoint_flush(lbm_handle h);
 int lbm_adjoint_init_velocity(lbm_handle h, const void *rho, const void *u0, int dtype,
                               const void *lambda0, void *grad_u0);
 int lbm_adjoint_tau_gradient(lbm_handle h, const double *grad_omega, double *dL_dtau);

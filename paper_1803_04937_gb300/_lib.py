@@ -23,6 +23,7 @@ OPT_WALLS_X, OPT_WALLS_Y, OPT_WALLS_Z = 5, 6, 7
 OPT_RHO0_MODE, OPT_PATTERN, OPT_TAU, OPT_EQUILIBRIUM, OPT_COLLISION = 8, 9, 10, 11, 12
 OPT_BLOCK_X, OPT_BLOCK_Y, OPT_CELLS_X = 13, 14, 15
 OPT_MRT_OMEGA_BULK, OPT_MRT_OMEGA_4, OPT_GRAPHS = 16, 17, 18
+OPT_ADJ_DEFER_SUM = 19
 RED_MASS, RED_ENERGY, RED_JX, RED_JY, RED_JZ, RED_UMAX, RED_NONFINITE = range(7)
 RED_COUNT = 8
 
@@ -55,6 +56,7 @@ _SIGS = {
     "lbm_set_pdfs": (_i, [_vp, _vp]),
     "lbm_adjoint_seed": (_i, [_vp, _vp, _vp, _i, _vp]),
     "lbm_adjoint_step": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_adjoint_flush": (_i, [_vp]),
     "lbm_adjoint_init_velocity": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "lbm_adjoint_tau_gradient": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),

@@ -66,6 +66,8 @@ class _Run(torch.autograd.Function):
         grad_rho = grad_rho.to(grad_u.dtype).contiguous() if grad_rho is not None else None
         lam = [torch.empty(shape, dtype=lam_dtype, device=dev) for _ in range(2)]
         gw = torch.zeros(2, dtype=torch.float64, device=dev)
+        # each step's dL/domega terms are summed inside the next step's kernel (bitwise the same sums)
+        check(lib.lbm_set_option(h, _lib.OPT_ADJ_DEFER_SUM, 1.0), h)
         check(lib.lbm_adjoint_seed(h, _ptr(grad_rho), _ptr(grad_u), dt, _ptr(lam[0])), h)
         cur = 0
         ring = [torch.empty(shape, dtype=sim.storage_dtype, device=dev) for _ in range(min(every, nsteps) + 1)]
@@ -83,6 +85,7 @@ class _Run(torch.autograd.Function):
         grad_u0 = torch.empty_like(u0)
         check(lib.lbm_adjoint_init_velocity(h, _ptr(rho) if rho.numel() else None, _ptr(u0), _field_dtype(u0),
                                             _ptr(lam[cur]), _ptr(grad_u0)), h)
+        check(lib.lbm_adjoint_flush(h), h)
         gwh = gw.cpu()
         dtau = ctypes.c_double()
         check(lib.lbm_adjoint_tau_gradient(h, _dp(gwh), ctypes.byref(dtau)), h)

@@ -234,13 +234,106 @@ __device__ __forceinline__ void adjoint_cell(const R f[Q], const R mu[Q], const 
     }
 }
 
+// Fixed-order sum of the per-block partials of k_adjoint_step into
+// grad_omega: FP64 partials (FP64 storage) in FP64, the double-float partials
+// of the FP32 arithmetic in double-float, the result added to grad_omega in
+// FP64.  The order is that of ADJ_SUM_VIRT virtual threads: virtual thread v
+// adds partials v, v + ADJ_SUM_VIRT, v + 2 ADJ_SUM_VIRT, ... in turn; the 32
+// virtual threads of each virtual warp are reduced by one shuffle tree and the
+// 32 virtual-warp sums by one more.  A block of NT threads (a multiple of 32,
+// blockDim.x a multiple of 32) plays ADJ_SUM_VIRT / NT virtual threads per
+// thread with the same lanes, so the result is bitwise the same for every NT:
+// the sum can run as its own one-block kernel (NT = 1024) or in one block of
+// the next adjoint step (NT = 256, see lbm_adjoint_step with deferred sums).
+constexpr int ADJ_SUM_VIRT = 1024;
+
+struct AccD {
+    double a0, a1;
+};
+struct AccF {
+    DF a0, a1;
+};
+__device__ __forceinline__ void acc_add(AccD &a, const double2 &v)
+{
+    a.a0 += v.x;
+    a.a1 += v.y;
+}
+__device__ __forceinline__ void acc_add(AccF &a, const float4 &v)
+{
+    a.a0 = df_add(a.a0, DF{v.x, v.y});
+    a.a1 = df_add(a.a1, DF{v.z, v.w});
+}
+__device__ __forceinline__ AccD acc_warp_sum(AccD a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.a0 += __shfl_down_sync(0xffffffffu, a.a0, o);
+        a.a1 += __shfl_down_sync(0xffffffffu, a.a1, o);
+    }
+    return a;
+}
+__device__ __forceinline__ AccF acc_warp_sum(AccF a) { return AccF{df_warp_sum(a.a0), df_warp_sum(a.a1)}; }
+__device__ __forceinline__ void acc_store(double *g, const AccD &a)
+{
+    g[0] += a.a0;
+    g[1] += a.a1;
+}
+__device__ __forceinline__ void acc_store(double *g, const AccF &a)
+{
+    g[0] += (double)a.a0.hi + (double)a.a0.lo;
+    g[1] += (double)a.a1.hi + (double)a.a1.lo;
+}
+
+// U terms of each virtual thread are loaded together (their order of addition
+// does not change).  sh: ADJ_SUM_VIRT / 32 accumulators of shared memory.
+template <int NT, int U, typename P, typename A>
+__device__ __forceinline__ void sum_partials(const P *partial, long long nblocks, double *grad_omega, A *sh)
+{
+    constexpr int V = ADJ_SUM_VIRT / NT;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    A acc[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = A{};
+    for (long long j = 0; j < nblocks; j += (long long)U * ADJ_SUM_VIRT) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const long long b0 = j + t + k * NT;
+            P v[U];
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                const long long b = b0 + (long long)i * ADJ_SUM_VIRT;
+                if (b < nblocks) v[i] = partial[b];
+            }
+#pragma unroll
+            for (int i = 0; i < U; ++i)
+                if (b0 + (long long)i * ADJ_SUM_VIRT < nblocks) acc_add(acc[k], v[i]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = acc_warp_sum(acc[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) sh[warp + k * (NT / 32)] = acc[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const A a = acc_warp_sum(sh[lane]);
+        if (lane == 0) acc_store(grad_omega, a);
+    }
+}
+
 // Addressing as in the forward step kernels: plane base pointers from the
 // kernel parameters, nine wrapped row offsets per thread (Site), and no
 // bounce-back logic when the lattice is periodic (WALLS = false).
+// prev_partial (may be NULL): the partials of the previous adjoint step, whose
+// sum the first block adds to prev_grad after its own cells (deferred sums).
 template <typename T, typename L, bool WALLS>
 __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 : 4)
     k_adjoint_step(Planes<T> state, Planes<L> lam_next, Planes<L> lam, double *partial, Geo g,
-                   AdjConst<typename Storage<T>::R> p)
+                   AdjConst<typename Storage<T>::R> p, const double *prev_partial, long long prev_nblocks,
+                   double *prev_grad)
 {
     using R = typename Storage<T>::R;
     __shared__ typename Storage<T>::R shp[256], shm[256];  // compute precision
@@ -306,87 +399,35 @@ __global__ void __launch_bounds__(256, sizeof(typename Storage<T>::R) == 8 ? 2 :
             if (tid == 0) reinterpret_cast<float4 *>(partial)[b] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
         }
     }
+    if (prev_partial && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+        // the previous step has completed (stream order), its partials are visible
+        if constexpr (sizeof(R) == 8) {
+            __shared__ AccD sh[ADJ_SUM_VIRT / 32];
+            sum_partials<256, 2>(reinterpret_cast<const double2 *>(prev_partial), prev_nblocks, prev_grad, sh);
+        } else {
+            __shared__ AccF sh[ADJ_SUM_VIRT / 32];
+            sum_partials<256, 2>(reinterpret_cast<const float4 *>(prev_partial), prev_nblocks, prev_grad, sh);
+        }
+    }
     // the sum of the partials (launched as a programmatic dependent) may start
     // once every block has got here; it waits for this grid's memory itself
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Sum of the per-block partials of k_adjoint_step into grad_omega (fixed
-// order), one block of ADJ_FINAL_THREADS; each thread's loads are unrolled so
-// that they are in flight together.  FP64 partials (FP64 storage) are summed in
-// FP64; the double-float partials of the FP32 arithmetic in double-float, and
-// the result is added to grad_omega in FP64.  Summing the 8192 FP64 partials of
-// the 128^3 adjoint workload in FP64 on the one SM took 11 us, an eighth of
-// the step, because this GPU's FP64 pipe is narrow; double-float sums run on
-// the FP32 pipe.
-constexpr int ADJ_FINAL_THREADS = 1024;
-
-__global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final(const double2 *partial, long long nblocks,
-                                                                     double *grad_omega)
+// The sum of the per-block partials of one adjoint step as a kernel of its
+// own (one block of ADJ_SUM_VIRT threads, each thread's eight loads in flight
+// together): launched as a programmatic dependent of the step, or by
+// lbm_adjoint_flush.  Summing the 8192 partials of the 128^3 adjoint workload
+// in FP64 on the one SM took 11 us, an eighth of the step, because this GPU's
+// FP64 pipe is narrow; the double-float sums of the FP32 arithmetic run on the
+// FP32 pipe.
+template <typename P, typename A>
+__global__ void __launch_bounds__(ADJ_SUM_VIRT) k_adjoint_final(const P *partial, long long nblocks,
+                                                                double *grad_omega)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");  // k_adjoint_step has finished, its partials visible
-    __shared__ double sh[32];
-    double a0 = 0.0, a1 = 0.0;
-    long long b = threadIdx.x;
-    for (; b + 7 * ADJ_FINAL_THREADS < nblocks; b += 8 * ADJ_FINAL_THREADS) {
-        double2 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = partial[b + i * ADJ_FINAL_THREADS];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            a0 += v[i].x;
-            a1 += v[i].y;
-        }
-    }
-    for (; b < nblocks; b += ADJ_FINAL_THREADS) {
-        const double2 v = partial[b];
-        a0 += v.x;
-        a1 += v.y;
-    }
-    a0 = block_sum(a0, sh);
-    a1 = block_sum(a1, sh);
-    if (threadIdx.x == 0) {
-        grad_omega[0] += a0;
-        grad_omega[1] += a1;
-    }
-}
-
-__global__ void __launch_bounds__(ADJ_FINAL_THREADS) k_adjoint_final_df(const float4 *partial, long long nblocks,
-                                                                        double *grad_omega)
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");  // k_adjoint_step has finished, its partials visible
-    __shared__ float4 sh[ADJ_FINAL_THREADS / 32];
-    DF a0{0.f, 0.f}, a1{0.f, 0.f};
-    long long b = threadIdx.x;
-    for (; b + 7 * ADJ_FINAL_THREADS < nblocks; b += 8 * ADJ_FINAL_THREADS) {
-        float4 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = partial[b + i * ADJ_FINAL_THREADS];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            a0 = df_add(a0, DF{v[i].x, v[i].y});
-            a1 = df_add(a1, DF{v[i].z, v[i].w});
-        }
-    }
-    for (; b < nblocks; b += ADJ_FINAL_THREADS) {
-        const float4 v = partial[b];
-        a0 = df_add(a0, DF{v.x, v.y});
-        a1 = df_add(a1, DF{v.z, v.w});
-    }
-    a0 = df_warp_sum(a0);
-    a1 = df_warp_sum(a1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sh[warp] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
-    __syncthreads();
-    if (warp == 0) {
-        const float4 v = lane < (int)(blockDim.x >> 5) ? sh[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        a0 = df_warp_sum(DF{v.x, v.y});
-        a1 = df_warp_sum(DF{v.z, v.w});
-        if (lane == 0) {
-            grad_omega[0] += (double)a0.hi + (double)a0.lo;
-            grad_omega[1] += (double)a1.hi + (double)a1.lo;
-        }
-    }
+    __shared__ A sh[ADJ_SUM_VIRT / 32];
+    sum_partials<ADJ_SUM_VIRT, 8>(partial, nblocks, grad_omega, sh);
 }
 
 template <typename In, typename L, typename R>
@@ -418,28 +459,35 @@ cudaError_t launch_adjoint_seed(int prec, const void *grad_rho, const void *grad
     return cudaGetLastError();
 }
 
+// One adjoint step.  partial: this step's block partials.  defer: leave them
+// for the next step's first block (prev_partial / prev_grad of that launch) or
+// for launch_adjoint_flush instead of summing them at once.
 template <typename T, typename L>
-static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam, double *grad_omega, double *scratch,
-                              const Geo &g, const CollBoth &cb, cudaStream_t s)
+static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam, double *grad_omega, double *partial,
+                              const double *prev_partial, double *prev_grad, bool defer, const Geo &g,
+                              const CollBoth &cb, cudaStream_t s)
 {
     using R = typename Storage<T>::R;
     AdjConst<R> p = to_adj<R>(cb);
     const Planes<T> S = planes_of<T>(const_cast<void *>(state), g.ncell);
     const Planes<L> Ln = planes_of<L>(const_cast<void *>(lam_next), g.ncell);
     const Planes<L> Lo = planes_of<L>(lam, g.ncell);
+    const long long nb = adjoint_blocks(g);
     if (g.wall_x || g.wall_y || g.wall_z)
-        k_adjoint_step<T, L, true><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, scratch, g, p);
+        k_adjoint_step<T, L, true><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, partial, g, p, prev_partial, nb,
+                                                                      prev_grad);
     else
-        k_adjoint_step<T, L, false><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, scratch, g, p);
+        k_adjoint_step<T, L, false><<<adj_grid(g), adj_block(), 0, s>>>(S, Ln, Lo, partial, g, p, prev_partial, nb,
+                                                                       prev_grad);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || defer) return e;
     // The final sum is a programmatic dependent launch: it is scheduled while
     // the step kernel's last blocks run (griddepcontrol.launch_dependents) and
     // waits inside for the step's completion (griddepcontrol.wait), which hides
     // the launch gap between the two.
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, 1, 1);
-    cfg.blockDim = dim3(ADJ_FINAL_THREADS, 1, 1);
+    cfg.blockDim = dim3(ADJ_SUM_VIRT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -447,25 +495,42 @@ static cudaError_t adj_step_t(const void *state, const void *lam_next, void *lam
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const long long nb = adjoint_blocks(g);
     if (sizeof(R) == 8)
-        e = cudaLaunchKernelEx(&cfg, k_adjoint_final, reinterpret_cast<const double2 *>(scratch), nb, grad_omega);
+        e = cudaLaunchKernelEx(&cfg, k_adjoint_final<double2, AccD>, reinterpret_cast<const double2 *>(partial), nb,
+                               grad_omega);
     else
-        e = cudaLaunchKernelEx(&cfg, k_adjoint_final_df, reinterpret_cast<const float4 *>(scratch), nb, grad_omega);
+        e = cudaLaunchKernelEx(&cfg, k_adjoint_final<float4, AccF>, reinterpret_cast<const float4 *>(partial), nb,
+                               grad_omega);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_step(int prec, const void *state, const void *lam_next, void *lam, double *grad_omega,
-                                double *scratch, const Geo &g, const CollBoth &c, cudaStream_t s)
+                                double *partial, const double *prev_partial, double *prev_grad, bool defer,
+                                const Geo &g, const CollBoth &c, cudaStream_t s)
 {
+#define LBM_ADJ_ARGS state, lam_next, lam, grad_omega, partial, prev_partial, prev_grad, defer, g, c, s
     switch (prec) {
-    case P_F64: return adj_step_t<double, double>(state, lam_next, lam, grad_omega, scratch, g, c, s);
-    case P_F32: return adj_step_t<float, float>(state, lam_next, lam, grad_omega, scratch, g, c, s);
-    case P_F16: return adj_step_t<__half, float>(state, lam_next, lam, grad_omega, scratch, g, c, s);
-    case P_BF16: return adj_step_t<__nv_bfloat16, float>(state, lam_next, lam, grad_omega, scratch, g, c, s);
+    case P_F64: return adj_step_t<double, double>(LBM_ADJ_ARGS);
+    case P_F32: return adj_step_t<float, float>(LBM_ADJ_ARGS);
+    case P_F16: return adj_step_t<__half, float>(LBM_ADJ_ARGS);
+    case P_BF16: return adj_step_t<__nv_bfloat16, float>(LBM_ADJ_ARGS);
     }
+#undef LBM_ADJ_ARGS
     return cudaErrorInvalidValue;
+}
+
+// Sums the deferred partials of an adjoint step into grad_omega.
+cudaError_t launch_adjoint_flush(int prec, const double *partial, double *grad_omega, const Geo &g, cudaStream_t s)
+{
+    const long long nb = adjoint_blocks(g);
+    if (prec == P_F64)
+        k_adjoint_final<double2, AccD><<<1, ADJ_SUM_VIRT, 0, s>>>(reinterpret_cast<const double2 *>(partial), nb,
+                                                                 grad_omega);
+    else
+        k_adjoint_final<float4, AccF><<<1, ADJ_SUM_VIRT, 0, s>>>(reinterpret_cast<const float4 *>(partial), nb,
+                                                                grad_omega);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_init_velocity(int prec, const void *rho, const void *u0, int dtype, const void *lam0,

@@ -34,6 +34,12 @@ struct lbm_ctx {
     int cur = 0;     // A/B: 0 -> a holds the current state, 1 -> b
     int parity = 0;  // AA: number of AA steps since init, mod 2
     long long t = 0;
+    // adjoint sums (LBM_OPT_ADJ_DEFER_SUM): the step whose block partials wait in
+    // scratch buffer adj_buf to be added to adj_pending_grad
+    int adj_defer = 0;
+    bool adj_pending = false;
+    int adj_buf = 0;
+    double *adj_pending_grad = nullptr;
     std::string err;
 };
 
@@ -118,8 +124,22 @@ size_t scratch_doubles(const lbm_ctx *h)
 {
     lbm::Geo g = geo(h);
     size_t red = (size_t)lbm::reduce_blocks() * 8 + 8;
-    size_t adj = (size_t)lbm::adjoint_blocks(g) * 2;
+    size_t adj = (size_t)lbm::adjoint_blocks(g) * 2 * 2;  // two buffers of block partials (deferred sums)
     return red > adj ? red : adj;
+}
+
+// Block-partial buffer i of the adjoint step in scratch.
+double *adj_partials(const lbm_ctx *h, int i) { return h->scratch + (size_t)i * 2 * lbm::adjoint_blocks(geo(h)); }
+
+// Adds a deferred adjoint step's partials to its grad_omega (LBM_OPT_ADJ_DEFER_SUM).
+int adj_flush(lbm_ctx *h, const char *where)
+{
+    if (!h->adj_pending) return LBM_OK;
+    h->adj_pending = false;
+    cudaError_t e = lbm::launch_adjoint_flush(h->precision, adj_partials(h, h->adj_buf), h->adj_pending_grad, geo(h),
+                                              h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, where);
+    return LBM_OK;
 }
 
 int check_ready(lbm_handle h)
@@ -373,6 +393,12 @@ int lbm_set_option(lbm_handle h, int key, double v)
         if (v != 0.0 && v != 1.0) return fail(h, LBM_EINVAL, "graphs option must be 0 or 1");
         h->graphs = (int)v;
         return LBM_OK;
+    case LBM_OPT_ADJ_DEFER_SUM: {
+        if (v != 0.0 && v != 1.0) return fail(h, LBM_EINVAL, "deferred adjoint sums option must be 0 or 1");
+        const int st = adj_flush(h, "lbm_set_option (adjoint flush)");
+        h->adj_defer = (int)v;
+        return st;
+    }
     case LBM_OPT_CELLS_X:
         if (v != 1.0 && v != 2.0 && v != 4.0) return fail(h, LBM_EINVAL, "cells per thread must be 1, 2 or 4");
         h->cells_x = (int)v;
@@ -411,6 +437,7 @@ int lbm_get_option(lbm_handle h, int key, double *v)
     case LBM_OPT_MRT_OMEGA_4: *v = h->omega_4; return LBM_OK;
     case LBM_OPT_CELLS_X: *v = h->cells_x; return LBM_OK;
     case LBM_OPT_GRAPHS: *v = h->graphs; return LBM_OK;
+    case LBM_OPT_ADJ_DEFER_SUM: *v = h->adj_defer; return LBM_OK;
     case LBM_OPT_BLOCK_X: *v = h->bx; return LBM_OK;
     case LBM_OPT_BLOCK_Y: *v = h->by; return LBM_OK;
     }
@@ -434,6 +461,8 @@ int lbm_bind(lbm_handle h, void *pdf_a, void *pdf_b, void *scratch, void *stream
     if (h->pattern == LBM_PATTERN_AB && pdf_a == pdf_b) return fail(h, LBM_EINVAL, "pdf_a and pdf_b must differ");
     if (!aligned(pdf_a) || (pdf_b && !aligned(pdf_b)) || (scratch && !aligned(scratch)))
         return fail(h, LBM_EINVAL, "device buffers must be 256-byte aligned");
+    const int st = adj_flush(h, "lbm_bind (adjoint flush)");  // pending partials live in the old scratch
+    if (st) return st;
     drop_graphs(h);  // captured kernels carry the old grid pointers
     h->a = pdf_a;
     h->b = h->pattern == LBM_PATTERN_AB ? pdf_b : nullptr;
@@ -532,6 +561,7 @@ int lbm_reduce(lbm_handle h, double *out)
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
     if (!h->scratch) return fail(h, LBM_ESTATE, "lbm_reduce needs a scratch buffer (lbm_bind)");
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
+    if ((s = adj_flush(h, "lbm_reduce (adjoint flush)"))) return s;  // the reduction reuses the scratch
     double *result = h->scratch + (size_t)lbm::reduce_blocks() * 8;
     cudaError_t e = lbm::launch_reduce(h->precision, layout(h), current(h), h->scratch, result, geo(h), coll(h),
                                        h->stream);
@@ -552,6 +582,7 @@ int lbm_enstrophy(lbm_handle h, double *out)
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
     if (!h->scratch) return fail(h, LBM_ESTATE, "lbm_enstrophy needs a scratch buffer (lbm_bind)");
     if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised");
+    if ((s = adj_flush(h, "lbm_enstrophy (adjoint flush)"))) return s;  // the reduction reuses the scratch
     double *result = h->scratch + (size_t)lbm::reduce_blocks() * 8;
     cudaError_t e = lbm::launch_enstrophy(h->precision, layout(h), current(h), h->scratch, result, geo(h), coll(h),
                                           h->stream);
@@ -635,6 +666,7 @@ int lbm_adjoint_seed(lbm_handle h, const void *grad_rho, const void *grad_u, int
     if ((s = check_dtype(h, dtype))) return s;
     if (h->rho0_mode) return fail(h, LBM_EUNSUPPORTED, "adjoint supports rho0 = 1 only");
     if (!grad_u || !lambda) return fail(h, LBM_EINVAL, "grad_u and lambda are required");
+    if ((s = adj_flush(h, "lbm_adjoint_seed (adjoint flush)"))) return s;
     cudaError_t e = lbm::launch_adjoint_seed(h->precision, grad_rho, grad_u, dtype, lambda, geo(h), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_adjoint_seed");
     return LBM_OK;
@@ -650,10 +682,30 @@ int lbm_adjoint_step(lbm_handle h, const void *state_t, const void *lambda_next,
     if (!state_t || !lambda_next || !lambda_t || !grad_omega) return fail(h, LBM_EINVAL, "null argument");
     if (lambda_next == lambda_t) return fail(h, LBM_EINVAL, "lambda_next and lambda_t must differ");
     if (!h->scratch) return fail(h, LBM_ESTATE, "lbm_adjoint_step needs a scratch buffer (lbm_bind)");
-    cudaError_t e = lbm::launch_adjoint_step(h->precision, state_t, lambda_next, lambda_t, grad_omega, h->scratch,
-                                             geo(h), coll(h), h->stream);
+    cudaError_t e;
+    if (!h->adj_defer) {
+        e = lbm::launch_adjoint_step(h->precision, state_t, lambda_next, lambda_t, grad_omega, adj_partials(h, 0),
+                                     nullptr, nullptr, false, geo(h), coll(h), h->stream);
+    } else {
+        // this step's partials go to the other buffer; the pending step's are summed by this step's first block
+        const int buf = h->adj_pending ? 1 - h->adj_buf : 0;
+        e = lbm::launch_adjoint_step(h->precision, state_t, lambda_next, lambda_t, grad_omega, adj_partials(h, buf),
+                                     h->adj_pending ? adj_partials(h, h->adj_buf) : nullptr,
+                                     h->adj_pending ? h->adj_pending_grad : nullptr, true, geo(h), coll(h),
+                                     h->stream);
+        h->adj_pending = e == cudaSuccess;
+        h->adj_buf = buf;
+        h->adj_pending_grad = grad_omega;
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_adjoint_step");
     return LBM_OK;
+}
+
+int lbm_adjoint_flush(lbm_handle h)
+{
+    int s = check_ready(h);
+    if (s) return s;
+    return adj_flush(h, "lbm_adjoint_flush");
 }
 
 int lbm_adjoint_init_velocity(lbm_handle h, const void *rho, const void *u0, int dtype, const void *lambda0,

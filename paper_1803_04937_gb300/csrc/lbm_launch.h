@@ -75,8 +75,14 @@ int velocity_set27(int *c, double *w, int *opp);
 int adjoint_blocks(const Geo &g);
 cudaError_t launch_adjoint_seed(int prec, const void *grad_rho, const void *grad_u, int dtype, void *lambda,
                                 const Geo &g, cudaStream_t stream);
+// partial: this step's block partials (adjoint_blocks(g) x 2 doubles); prev_partial / prev_grad (may be NULL):
+// a deferred step's partials, summed into prev_grad by this step's first block; defer: leave this step's
+// partials for the next step or launch_adjoint_flush instead of summing them into grad_omega at once.
 cudaError_t launch_adjoint_step(int prec, const void *state, const void *lam_next, void *lam, double *grad_omega,
-                                double *scratch, const Geo &g, const CollBoth &c, cudaStream_t stream);
+                                double *partial, const double *prev_partial, double *prev_grad, bool defer,
+                                const Geo &g, const CollBoth &c, cudaStream_t stream);
+cudaError_t launch_adjoint_flush(int prec, const double *partial, double *grad_omega, const Geo &g,
+                                 cudaStream_t stream);
 cudaError_t launch_adjoint_init_velocity(int prec, const void *rho, const void *u0, int dtype, const void *lam0,
                                          void *grad_u0, const Geo &g, const CollBoth &c, cudaStream_t stream);
 

@@ -118,3 +118,53 @@ def test_adjoint_128cube_against_finite_differences():
     fdt = (loss(u0, 0.7 + ht) - loss(u0, 0.7 - ht)) / (2 * ht)
     print("dL/dtau: adjoint %.9e, FD %.9e" % (float(tau.grad), fdt))
     assert float(tau.grad) == pytest.approx(fdt, rel=1e-3)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("shape,walls", [((33, 40, 130), (False, False, False)), ((130, 128, 64), (False, False, False)),
+                                         ((9, 14, 40), (False, True, True))])
+def test_deferred_adjoint_sums_are_bitwise_the_immediate_ones(shape, walls, precision):
+    """LBM_OPT_ADJ_DEFER_SUM: each step's dL/domega partials summed by the next
+    step's first block (256 threads) or by lbm_adjoint_flush give bitwise the
+    sums of the one-block kernel (1024 threads) after every step, and the same
+    lambdas; lbm_reduce flushes a pending sum first.  The lattices give 1320
+    and 8320 block partials (one and two passes of the 1024-thread loop) and a
+    walled one."""
+    import ctypes
+
+    from paper_1803_04937_gb300 import _lib
+    from paper_1803_04937_gb300.lbm import Simulation
+    nz, ny, nx = shape
+    dt = torch.float64 if precision == "f64" else torch.float32
+    rho, u = random_fields(shape, seed=61)
+    gen = torch.Generator().manual_seed(62)
+    lam0 = (torch.rand((19,) + tuple(shape), generator=gen, dtype=torch.float64) - 0.5).to("cuda", dt)
+    steps = 5
+    out = {}
+    for defer in (0, 1):
+        sim = Simulation(nx, ny, nz, precision=precision, equilibrium="improved", collision="trt", tau=0.6,
+                         walls=walls, force=(1e-4, 0.0, -5e-5))
+        sim.init(rho.cuda(), u.cuda())
+        lib, h = sim._lib, sim.handle
+        _lib.check(lib.lbm_set_option(h, _lib.OPT_ADJ_DEFER_SUM, float(defer)), h)
+        lam = [lam0.clone(), torch.empty_like(lam0)]
+        gws = [torch.zeros(2, dtype=torch.float64, device="cuda") for _ in range(steps)]
+        state = ctypes.c_void_p(sim.grids[0].data_ptr())
+        for i in range(steps):
+            # every step adds to its own accumulator, so each step's sum is checked
+            _lib.check(lib.lbm_adjoint_step(h, state, ctypes.c_void_p(lam[i % 2].data_ptr()),
+                                            ctypes.c_void_p(lam[1 - i % 2].data_ptr()),
+                                            ctypes.cast(ctypes.c_void_p(gws[i].data_ptr()),
+                                                        ctypes.POINTER(ctypes.c_double))), h)
+            if i == 2:
+                sim.reduce()  # flushes the pending sum of step 2
+                torch.cuda.synchronize()
+                assert gws[2].abs().sum().item() > 0
+        _lib.check(lib.lbm_adjoint_flush(h), h)
+        torch.cuda.synchronize()
+        out[defer] = (torch.stack(gws).cpu(), lam[steps % 2].cpu())
+        sim.close()
+    print("deferred adjoint sums %s %s: %s" % (precision, shape, out[1][0][:, 0].tolist()))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    assert (out[0][0] != 0).all()
