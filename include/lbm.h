@@ -126,8 +126,9 @@ typedef struct lbm_ctx *lbm_handle;
                                  (in the first block of its kernel) or by lbm_adjoint_flush,
                                  which takes a one-block kernel off each step's critical path.
                                  Bitwise the same sums either way.  Changing the option,
-                                 lbm_bind, lbm_reduce, lbm_enstrophy and lbm_adjoint_seed
-                                 flush first; lbm_destroy drops a pending sum. */
+                                 lbm_bind with another scratch buffer or stream, lbm_reduce,
+                                 lbm_enstrophy and lbm_adjoint_seed flush first; lbm_destroy
+                                 drops a pending sum. */
 
 /* lbm_reduce output slots */
 #define LBM_RED_MASS      0   /* sum_x rho */

@@ -461,8 +461,10 @@ int lbm_bind(lbm_handle h, void *pdf_a, void *pdf_b, void *scratch, void *stream
     if (h->pattern == LBM_PATTERN_AB && pdf_a == pdf_b) return fail(h, LBM_EINVAL, "pdf_a and pdf_b must differ");
     if (!aligned(pdf_a) || (pdf_b && !aligned(pdf_b)) || (scratch && !aligned(scratch)))
         return fail(h, LBM_EINVAL, "device buffers must be 256-byte aligned");
-    const int st = adj_flush(h, "lbm_bind (adjoint flush)");  // pending partials live in the old scratch
-    if (st) return st;
+    if ((double *)scratch != h->scratch || (cudaStream_t)stream != h->stream) {
+        const int st = adj_flush(h, "lbm_bind (adjoint flush)");  // pending partials live in the old scratch
+        if (st) return st;
+    }
     drop_graphs(h);  // captured kernels carry the old grid pointers
     h->a = pdf_a;
     h->b = h->pattern == LBM_PATTERN_AB ? pdf_b : nullptr;
