@@ -144,5 +144,11 @@ def test_graph_and_block_options_on_host(lib):
         assert lib.lbm_set_option(h, _lib.OPT_TAU, 0.5) == _lib.LBM_EINVAL
         assert lib.lbm_set_option(h, _lib.OPT_TAU, float("nan")) == _lib.LBM_EINVAL
         assert lib.lbm_step(h, -1) in (_lib.LBM_EINVAL, _lib.LBM_ESTATE)
+        # deferred adjoint sums: 0 or 1, default 0; nothing is pending on an unbound handle
+        assert lib.lbm_get_option(h, _lib.OPT_ADJ_DEFER_SUM, ctypes.byref(v)) == 0 and v.value == 0.0
+        assert lib.lbm_set_option(h, _lib.OPT_ADJ_DEFER_SUM, 2.0) == _lib.LBM_EINVAL
+        assert lib.lbm_set_option(h, _lib.OPT_ADJ_DEFER_SUM, 1.0) == 0
+        assert lib.lbm_get_option(h, _lib.OPT_ADJ_DEFER_SUM, ctypes.byref(v)) == 0 and v.value == 1.0
+        assert lib.lbm_adjoint_flush(h) == _lib.LBM_ESTATE  # no bound memory
     finally:
         lib.lbm_destroy(h)
