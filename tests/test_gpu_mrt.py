@@ -79,9 +79,11 @@ def test_mrt_16bit_storage_error(case, precision, tol):
 
 
 @pytest.mark.parametrize("precision", ["f32", "f16s", "f64"])
-@pytest.mark.parametrize("case", [1, 3])
+@pytest.mark.parametrize("case", [1, 2, 3, 4, 5])
 def test_mrt_aa_equals_ab_bitwise(case, precision):
-    """AA and A/B run the same MRT arithmetic per cell: identical bits."""
+    """AA and A/B run the same MRT arithmetic per cell: identical bits, also
+    with the walled AA odd step split into interior and wall rows (walls on y,
+    on z, on x only, and on all axes)."""
     kw = CASES[case]
     shape = (6, 11, 45)
     rho, u = random_fields(shape, seed=5)
