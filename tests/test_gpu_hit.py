@@ -1,10 +1,12 @@
 """Decaying homogeneous isotropic turbulence: periodic 768^3, tau = 0.51, SRT,
 solenoidal initial field with E(k) ~ k^4 exp(-2 (k/4)^2), u_rms = 0.04
 (seed 4), 2000 steps, FP16-shifted vs FP32 storage, both equilibria.  The flow
-is chaotic, so the 768^3 runs are not compared point by point with the oracle
-(parity unpinned at this size); instead the same seed at 192^3 runs in FP64 on
-the GPU, which is pinned to the CPU oracle for 200 steps, and the 16- and
-32-bit storage runs are compared with it (energy and enstrophy series).
+is chaotic, so the 768^3 trajectories are not compared point by point with the
+oracle; at 768^3 the one-step update of sampled cells from the GPU's own state
+is (test_hit_768_one_step_matches_oracle_on_sampled_cells), and the same seed
+at 192^3 runs in FP64 on the GPU, which is pinned to the CPU oracle for 200
+steps, and the 16- and 32-bit storage runs are compared with it (energy and
+enstrophy series).
 
 At 768^3 D3Q19-I becomes non-finite and D3Q19-S does not.  The cause is the
 scheme, not the storage: linearised about a uniform flow, SRT at tau = 0.51
@@ -169,3 +171,81 @@ def test_uniform_flow_growth_rate_on_the_gpu():
           % (["%.1e" % x for x in amp["standard"]], ["%.1e" % x for x in amp["improved"]], rate, np.log(g)))
     assert rate == pytest.approx(np.log(g), rel=0.03)
     assert amp["standard"][4] <= amp["standard"][0]
+
+
+# Absolute slack beside half an ulp of the stored value: the FP32 arithmetic of
+# the collision (the GPU rounds its FP32 result, the oracle computes in FP64).
+# Measured largest differences: FP32 1.0e-8 (0.5 of the bound below), FP16
+# 7.58e-6, i.e. 0.99 of half an ulp at the largest populations.
+SLACK = {"f32": 2e-8, "f16s": 1e-7}
+
+
+def _patches_and_centres(f, zs, ys, xs):
+    """3x3x3 periodic neighbourhoods [S, Q, 3, 3, 3] of the cells (zs, ys, xs)
+    of a canonical population tensor f[Q, nz, ny, nx] (on the device), as
+    float64 on the host."""
+    _, nz, ny, nx = f.shape
+    d = torch.tensor([-1, 0, 1], device=f.device)
+    Z = (zs[:, None, None, None] + d[None, :, None, None]) % nz
+    Y = (ys[:, None, None, None] + d[None, None, :, None]) % ny
+    X = (xs[:, None, None, None] + d[None, None, None, :]) % nx
+    return f[:, Z, Y, X].permute(1, 0, 2, 3, 4).double().cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,pattern,equilibrium", [("f32", "aa", "improved"), ("f16s", "aa", "improved"),
+                                                           ("f16s", "ab", "improved"), ("f32", "aa", "standard")])
+def test_hit_768_one_step_matches_oracle_on_sampled_cells(precision, pattern, equilibrium):
+    """The decaying-turbulence workload at its full size (768^3, tau = 0.51,
+    SRT, the bench's storage and pattern), in the launch configuration the
+    bench times: from the GPU's own state after 9 and after 10 steps (both AA
+    parities), the next GPU step of 192 sampled cells (random, plus cells on
+    the lattice's faces, edges and corners) equals the FP64 oracle's step of a
+    3 x 3 x 3 periodic neighbourhood of each (the centre cell of such a patch
+    pulls only from the patch) to within the rounding of the storage type:
+    half a unit in the last place of the stored shifted value, plus the FP32
+    arithmetic for FP32 storage."""
+    from paper_1803_04937_gb300.lbm import Simulation
+    from tests._helpers import gpu_to_oracle_order
+    n = 768
+    sim = Simulation(n, n, n, equilibrium=equilibrium, collision="srt", tau=0.51, precision=precision, pattern=pattern)
+    _, u = inputs.hit_spectrum(n, n, n, u_rms=0.04, seed=4, device="cuda")
+    sim.init(None, u.float())
+    del u
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(77)
+    pts = [rng.integers(0, n, 3) for _ in range(160)]
+    pts += [np.array([a, b, c]) for a in (0, n - 1) for b in (0, n - 1) for c in (0, n - 1)]  # corners
+    pts += [np.array([0, rng.integers(0, n), rng.integers(0, n)]) for _ in range(8)]
+    pts += [np.array([rng.integers(0, n), n - 1, rng.integers(0, n)]) for _ in range(8)]
+    pts += [np.array([rng.integers(0, n), rng.integers(0, n), 0]) for _ in range(8)]
+    pts = np.array(pts)  # [S, 3] as (z, y, x)
+    zs, ys, xs = (torch.tensor(pts[:, i], device="cuda") for i in range(3))
+    perm = gpu_to_oracle_order(19)
+    _, w, _ = oracle.velocity_set(19)
+    cfg = oracle_config(3, 3, 3, equilibrium=equilibrium, collision="srt", tau=0.51)
+    st = np.float32 if precision == "f32" else np.float16
+    sim.step(9)
+    worst = worst_abs = 0.0
+    for _ in range(2):
+        f0 = sim.get_pdfs()
+        patches = _patches_and_centres(f0, zs, ys, xs)  # [S, Q, 3, 3, 3], shifted, GPU order
+        del f0
+        torch.cuda.empty_cache()
+        sim.step(1)
+        f1 = sim.get_pdfs()
+        got = f1[:, zs, ys, xs].double().cpu().numpy().T  # [S, Q], shifted, GPU order
+        del f1
+        torch.cuda.empty_cache()
+        for s in range(len(pts)):
+            fo = np.moveaxis(patches[s][perm], 0, -1) + w  # [3, 3, 3, Q] unshifted, oracle order
+            want = oracle.step(cfg, fo, 1)[1, 1, 1] - w  # shifted, oracle order
+            g = got[s][perm]
+            ulp = np.spacing(np.maximum(np.abs(g), np.abs(want)).astype(st)).astype(np.float64)
+            err = np.abs(g - want) / (0.5 * ulp + SLACK[precision])
+            worst = max(worst, float(err.max()))
+            worst_abs = max(worst_abs, float(np.abs(g - want).max()))
+    sim.close()
+    torch.cuda.empty_cache()
+    print("HIT 768^3 %s %s %s: one-step error on %d sampled cells, in units of (half an ulp of the storage + slack): "
+          "max %.3f (largest absolute difference %.3e)" % (precision, pattern, equilibrium, len(pts), worst, worst_abs))
+    assert worst <= 1.0 + 1e-9
