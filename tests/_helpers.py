@@ -120,3 +120,74 @@ def srt_max_amplification(U, improved, tau, n):
     ph = np.exp(-1j * (kk @ c.T))  # [nk, Q]
     G = ph[:, :, None] * J[None, :, :]
     return float(np.abs(np.linalg.eigvals(G)).max())
+
+
+# ---------------------------------------------------------------- one step of sampled cells at full size
+
+def _storage_spacing(v, precision):
+    """Spacing of the storage type at |v| (float64 array)."""
+    a = np.abs(v)
+    if precision == "f32":
+        return np.spacing(a.astype(np.float32)).astype(np.float64)
+    if precision == "f16s":
+        return np.spacing(a.astype(np.float16)).astype(np.float64)
+    if precision == "bf16s":  # 8 significant bits: 2^16 times the float32 spacing
+        return np.spacing(a.astype(np.float32)).astype(np.float64) * 65536.0
+    return np.spacing(a)
+
+
+def _axis_patch(c, n, walled):
+    """Rows of a patch around coordinate c along an axis of n cells, the index
+    of c in it, and whether the patch is walled along that axis: next to a wall
+    the two cells at the wall (walls at both patch ends; only the one the centre
+    touches matters), else the three cells c - 1, c, c + 1 (periodic wrap)."""
+    if walled and n == 1:
+        return [c], 0, True
+    if walled and c == 0:
+        return [0, 1], 0, True
+    if walled and c == n - 1:
+        return [n - 2, n - 1], 1, True
+    return [(c - 1) % n, c, (c + 1) % n], 1, False
+
+
+def one_step_sampled_errors(sim, pts, kw, precision, slack):
+    """Runs one GPU step of `sim` (D3Q19, no walls on x) and compares it, at the
+    cells pts[S] = (z, y, x), with the FP64 oracle's step of each cell's
+    neighbourhood taken from the GPU's state before the step: the centre of a
+    patch pulls only from the patch, so the oracle's step of the patch is the
+    exact step of that cell.  Returns (largest difference in units of half an
+    ulp of the stored shifted value plus `slack`, largest absolute difference)."""
+    assert not kw.get("walls", (False, False, False))[0]
+    walls = kw.get("walls", (False, False, False))
+    nz, ny, nx = sim.shape
+    perm = gpu_to_oracle_order(19)
+    _, w, _ = oracle.velocity_set(19)
+    f0 = sim.get_pdfs()
+    patches = []
+    for z, y, x in pts:
+        zr, zc, zw = _axis_patch(int(z), nz, walls[2])
+        yr, yc, yw = _axis_patch(int(y), ny, walls[1])
+        xr, xc, _ = _axis_patch(int(x), nx, False)
+        idx = [torch.tensor(r, device=f0.device) for r in (zr, yr, xr)]
+        p = f0[:, idx[0][:, None, None], idx[1][None, :, None], idx[2][None, None, :]].double().cpu().numpy()
+        patches.append((p, (zc, yc, xc), (zw, yw)))
+    del f0
+    torch.cuda.empty_cache()
+    sim.step(1)
+    f1 = sim.get_pdfs()
+    t = [torch.tensor([int(q[i]) for q in pts], device=f1.device) for i in range(3)]
+    got = f1[:, t[0], t[1], t[2]].double().cpu().numpy().T  # [S, Q] shifted, GPU order
+    del f1
+    torch.cuda.empty_cache()
+    worst = worst_abs = 0.0
+    for s, (p, (zc, yc, xc), (zw, yw)) in enumerate(patches):
+        pz, py, px = p.shape[1:]
+        cfg = oracle_config(px, py, pz, **dict(kw, walls=(False, yw, zw)))
+        fo = np.moveaxis(p[perm], 0, -1) + w
+        want = oracle.step(cfg, fo, 1)[zc, yc, xc] - w
+        g = got[s][perm]
+        d = np.abs(g - want)
+        unit = 0.5 * _storage_spacing(np.maximum(np.abs(g), np.abs(want)), precision) + slack
+        worst = max(worst, float((d / unit).max()))
+        worst_abs = max(worst_abs, float(d.max()))
+    return worst, worst_abs

@@ -180,18 +180,6 @@ def test_uniform_flow_growth_rate_on_the_gpu():
 SLACK = {"f32": 2e-8, "f16s": 1e-7}
 
 
-def _patches_and_centres(f, zs, ys, xs):
-    """3x3x3 periodic neighbourhoods [S, Q, 3, 3, 3] of the cells (zs, ys, xs)
-    of a canonical population tensor f[Q, nz, ny, nx] (on the device), as
-    float64 on the host."""
-    _, nz, ny, nx = f.shape
-    d = torch.tensor([-1, 0, 1], device=f.device)
-    Z = (zs[:, None, None, None] + d[None, :, None, None]) % nz
-    Y = (ys[:, None, None, None] + d[None, None, :, None]) % ny
-    X = (xs[:, None, None, None] + d[None, None, None, :]) % nx
-    return f[:, Z, Y, X].permute(1, 0, 2, 3, 4).double().cpu().numpy()
-
-
 @pytest.mark.parametrize("precision,pattern,equilibrium", [("f32", "aa", "improved"), ("f16s", "aa", "improved"),
                                                            ("f16s", "ab", "improved"), ("f32", "aa", "standard")])
 def test_hit_768_one_step_matches_oracle_on_sampled_cells(precision, pattern, equilibrium):
@@ -200,14 +188,14 @@ def test_hit_768_one_step_matches_oracle_on_sampled_cells(precision, pattern, eq
     bench times: from the GPU's own state after 9 and after 10 steps (both AA
     parities), the next GPU step of 192 sampled cells (random, plus cells on
     the lattice's faces, edges and corners) equals the FP64 oracle's step of a
-    3 x 3 x 3 periodic neighbourhood of each (the centre cell of such a patch
-    pulls only from the patch) to within the rounding of the storage type:
-    half a unit in the last place of the stored shifted value, plus the FP32
-    arithmetic for FP32 storage."""
+    3 x 3 x 3 periodic neighbourhood of each to within the rounding of the
+    storage type: half a unit in the last place of the stored shifted value,
+    plus the FP32 arithmetic (SLACK)."""
     from paper_1803_04937_gb300.lbm import Simulation
-    from tests._helpers import gpu_to_oracle_order
+    from tests._helpers import one_step_sampled_errors
     n = 768
-    sim = Simulation(n, n, n, equilibrium=equilibrium, collision="srt", tau=0.51, precision=precision, pattern=pattern)
+    kw = dict(equilibrium=equilibrium, collision="srt", tau=0.51)
+    sim = Simulation(n, n, n, precision=precision, pattern=pattern, **kw)
     _, u = inputs.hit_spectrum(n, n, n, u_rms=0.04, seed=4, device="cuda")
     sim.init(None, u.float())
     del u
@@ -218,34 +206,11 @@ def test_hit_768_one_step_matches_oracle_on_sampled_cells(precision, pattern, eq
     pts += [np.array([0, rng.integers(0, n), rng.integers(0, n)]) for _ in range(8)]
     pts += [np.array([rng.integers(0, n), n - 1, rng.integers(0, n)]) for _ in range(8)]
     pts += [np.array([rng.integers(0, n), rng.integers(0, n), 0]) for _ in range(8)]
-    pts = np.array(pts)  # [S, 3] as (z, y, x)
-    zs, ys, xs = (torch.tensor(pts[:, i], device="cuda") for i in range(3))
-    perm = gpu_to_oracle_order(19)
-    _, w, _ = oracle.velocity_set(19)
-    cfg = oracle_config(3, 3, 3, equilibrium=equilibrium, collision="srt", tau=0.51)
-    st = np.float32 if precision == "f32" else np.float16
     sim.step(9)
-    worst = worst_abs = 0.0
-    for _ in range(2):
-        f0 = sim.get_pdfs()
-        patches = _patches_and_centres(f0, zs, ys, xs)  # [S, Q, 3, 3, 3], shifted, GPU order
-        del f0
-        torch.cuda.empty_cache()
-        sim.step(1)
-        f1 = sim.get_pdfs()
-        got = f1[:, zs, ys, xs].double().cpu().numpy().T  # [S, Q], shifted, GPU order
-        del f1
-        torch.cuda.empty_cache()
-        for s in range(len(pts)):
-            fo = np.moveaxis(patches[s][perm], 0, -1) + w  # [3, 3, 3, Q] unshifted, oracle order
-            want = oracle.step(cfg, fo, 1)[1, 1, 1] - w  # shifted, oracle order
-            g = got[s][perm]
-            ulp = np.spacing(np.maximum(np.abs(g), np.abs(want)).astype(st)).astype(np.float64)
-            err = np.abs(g - want) / (0.5 * ulp + SLACK[precision])
-            worst = max(worst, float(err.max()))
-            worst_abs = max(worst_abs, float(np.abs(g - want).max()))
+    res = [one_step_sampled_errors(sim, pts, kw, precision, SLACK[precision]) for _ in range(2)]
     sim.close()
     torch.cuda.empty_cache()
+    worst, worst_abs = max(r[0] for r in res), max(r[1] for r in res)
     print("HIT 768^3 %s %s %s: one-step error on %d sampled cells, in units of (half an ulp of the storage + slack): "
           "max %.3f (largest absolute difference %.3e)" % (precision, pattern, equilibrium, len(pts), worst, worst_abs))
     assert worst <= 1.0 + 1e-9

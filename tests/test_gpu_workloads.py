@@ -175,6 +175,48 @@ def test_shear_wave_256_16bit(precision):
 CHANNEL_16BIT_ERR = {"f16s": 1.0 + 1e-6, "bf16s": 0.85}
 
 
+# Absolute slack beside half an ulp of the stored value in the sampled
+# one-step comparison (the FP32 arithmetic of the collision).
+ONE_STEP_SLACK = {"f32": 2e-8, "f16s": 1e-7, "bf16s": 1e-7}
+
+
+@pytest.mark.parametrize("precision,pattern", [("f32", "ab"), ("f16s", "ab"), ("bf16s", "ab"), ("f32", "aa"),
+                                               ("f16s", "aa")])
+def test_channel_512x256x256_one_step_on_a_random_state(precision, pattern):
+    """The walled channel's lattice and collision (512x256x256, walls at both y
+    ends, TRT 3/16, tau = 0.6, body force) at full size, with the bench's
+    kernels (interior rows through the periodic kernel, wall rows through the
+    walled one): from a random state (seeded rho in 1 +- 0.02, u in +-0.05,
+    three steps on), one GPU step of 256 sampled cells (random, on both walls,
+    and on the periodic x and z ends) equals the FP64 oracle's step of each
+    cell's neighbourhood (next to a wall: the two rows at the wall with walls in
+    the patch) to within half an ulp of the stored value plus the FP32
+    arithmetic, for both AA parities."""
+    from tests._helpers import one_step_sampled_errors
+    nx, ny, nz, tau = 512, 256, 256, 0.6
+    a = 8 * (tau - 0.5) / 3 * 0.05 / ny ** 2
+    kw = dict(equilibrium="improved", collision="trt", tau=tau, force=(a, 0, 0), walls=(False, True, False))
+    sim = _sim(nx, ny, nz, precision=precision, pattern=pattern, **kw)
+    gen = torch.Generator(device="cuda").manual_seed(91)
+    rho = 1 + 0.02 * (2 * torch.rand((nz, ny, nx), generator=gen, device="cuda") - 1)
+    u = 0.05 * (2 * torch.rand((3, nz, ny, nx), generator=gen, device="cuda") - 1)
+    sim.init(rho, u)
+    del rho, u
+    sim.step(3)
+    rng = np.random.default_rng(92)
+    pts = [np.array([rng.integers(0, nz), rng.integers(0, ny), rng.integers(0, nx)]) for _ in range(160)]
+    pts += [np.array([rng.integers(0, nz), yw, rng.integers(0, nx)]) for yw in (0, ny - 1) for _ in range(32)]
+    pts += [np.array([rng.integers(0, nz), rng.integers(0, ny), xe]) for xe in (0, nx - 1) for _ in range(8)]
+    pts += [np.array([ze, rng.integers(0, ny), rng.integers(0, nx)]) for ze in (0, nz - 1) for _ in range(8)]
+    res = [one_step_sampled_errors(sim, pts, kw, precision, ONE_STEP_SLACK[precision]) for _ in range(2)]
+    sim.close()
+    worst, worst_abs = max(r[0] for r in res), max(r[1] for r in res)
+    print("channel 512x256x256 %s %s, random state: one-step error on %d sampled cells, in units of (half an ulp "
+          "of the storage + slack): max %.3f (largest absolute difference %.3e)"
+          % (precision, pattern, len(pts), worst, worst_abs))
+    assert worst <= 1.0 + 1e-9
+
+
 @pytest.mark.parametrize("precision", ["f32", "f16s", "bf16s"])
 def test_channel_512x256x256(precision):
     """Walls at y = -1/2 and 255.5, periodic x, z, body force a_x = 8 nu u_c / H^2
