@@ -151,7 +151,7 @@ def _axis_patch(c, n, walled):
 
 
 def one_step_sampled_errors(sim, pts, kw, precision, slack):
-    """Runs one GPU step of `sim` (D3Q19, no walls on x) and compares it, at the
+    """Runs one GPU step of `sim` (D3Q19 or D3Q27, no walls on x) and compares it, at the
     cells pts[S] = (z, y, x), with the FP64 oracle's step of each cell's
     neighbourhood taken from the GPU's state before the step: the centre of a
     patch pulls only from the patch, so the oracle's step of the patch is the
@@ -160,8 +160,8 @@ def one_step_sampled_errors(sim, pts, kw, precision, slack):
     assert not kw.get("walls", (False, False, False))[0]
     walls = kw.get("walls", (False, False, False))
     nz, ny, nx = sim.shape
-    perm = gpu_to_oracle_order(19)
-    _, w, _ = oracle.velocity_set(19)
+    perm = gpu_to_oracle_order(sim.stencil)
+    _, w, _ = oracle.velocity_set(sim.stencil)
     f0 = sim.get_pdfs()
     patches = []
     for z, y, x in pts:
@@ -182,7 +182,7 @@ def one_step_sampled_errors(sim, pts, kw, precision, slack):
     worst = worst_abs = 0.0
     for s, (p, (zc, yc, xc), (zw, yw)) in enumerate(patches):
         pz, py, px = p.shape[1:]
-        cfg = oracle_config(px, py, pz, **dict(kw, walls=(False, yw, zw)))
+        cfg = oracle_config(px, py, pz, **dict(kw, walls=(False, yw, zw), stencil=sim.stencil))
         fo = np.moveaxis(p[perm], 0, -1) + w
         want = oracle.step(cfg, fo, 1)[zc, yc, xc] - w
         g = got[s][perm]

@@ -217,23 +217,24 @@ def test_channel_512x256x256_one_step_on_a_random_state(precision, pattern):
     assert worst <= 1.0 + 1e-9
 
 
-@pytest.mark.parametrize("precision,pattern,collision,equilibrium", [
-    ("f32", "ab", "srt", "improved"), ("f32", "ab", "trt", "standard"), ("f16s", "ab", "srt", "improved"),
-    ("bf16s", "aa", "trt", "improved"), ("f32", "aa", "mrt", "improved"), ("f16s", "ab", "mrt", "standard")])
-def test_periodic_256_one_step_on_a_random_state(precision, pattern, collision, equilibrium):
+@pytest.mark.parametrize("precision,pattern,collision,equilibrium,stencil", [
+    ("f32", "ab", "srt", "improved", 19), ("f32", "ab", "trt", "standard", 19), ("f16s", "ab", "srt", "improved", 19),
+    ("bf16s", "aa", "trt", "improved", 19), ("f32", "aa", "mrt", "improved", 19), ("f16s", "ab", "mrt", "standard", 19),
+    ("f32", "ab", "trt", "standard", 27), ("f16s", "ab", "srt", "standard", 27)])
+def test_periodic_256_one_step_on_a_random_state(precision, pattern, collision, equilibrium, stencil):
     """The benchmark's lattice (periodic 256^3) and launch configuration from a
     random state (seeded rho in 1 +- 0.02, u in +-0.05, three steps on): one
     GPU step of 192 sampled cells (random, and on the periodic faces and
     corners) equals the FP64 oracle's step of each cell's 3 x 3 x 3
     neighbourhood to within half an ulp of the stored value plus the FP32
     arithmetic, for SRT, TRT and MRT, both equilibria, A/B and both AA
-    parities."""
+    parities, and for the D3Q27 comparison lattice."""
     from tests._helpers import one_step_sampled_errors
     n, tau = 256, 0.8
     kw = dict(equilibrium=equilibrium, collision=collision, tau=tau)
     if collision == "mrt":
         kw.update(omega_bulk=1.3, omega_4=0.9)
-    sim = _sim(n, n, n, precision=precision, pattern=pattern, **kw)
+    sim = _sim(n, n, n, precision=precision, pattern=pattern, stencil=stencil, **kw)
     gen = torch.Generator(device="cuda").manual_seed(93)
     rho = 1 + 0.02 * (2 * torch.rand((n, n, n), generator=gen, device="cuda") - 1)
     u = 0.05 * (2 * torch.rand((3, n, n, n), generator=gen, device="cuda") - 1)
@@ -247,9 +248,9 @@ def test_periodic_256_one_step_on_a_random_state(precision, pattern, collision, 
     res = [one_step_sampled_errors(sim, pts, kw, precision, ONE_STEP_SLACK[precision]) for _ in range(2)]
     sim.close()
     worst, worst_abs = max(r[0] for r in res), max(r[1] for r in res)
-    print("periodic 256^3 %s %s %s %s, random state: one-step error on %d sampled cells, in units of (half an ulp "
-          "of the storage + slack): max %.3f (largest absolute difference %.3e)"
-          % (precision, pattern, collision, equilibrium, len(pts), worst, worst_abs))
+    print("periodic 256^3 D3Q%d %s %s %s %s, random state: one-step error on %d sampled cells, in units of (half an "
+          "ulp of the storage + slack): max %.3f (largest absolute difference %.3e)"
+          % (stencil, precision, pattern, collision, equilibrium, len(pts), worst, worst_abs))
     assert worst <= 1.0 + 1e-9
 
 
